@@ -1,0 +1,219 @@
+/*
+ * tripoll.h -- C ABI of the B300 metadata triangle survey library (libtripoll.so).
+ *
+ * The library computes surveys of triangles in decorated temporal graphs, the
+ * operation of TriPoll (Steil et al., arXiv 2107.12330): every triangle of an
+ * undirected graph is found exactly once in the degree-ordered directed graph
+ * G+ (Sec. 3) by intersecting out-lists (Sec. 4.3, Alg. 1), and the metadata of
+ * each triangle -- three vertex labels, three edge timestamps, three edge
+ * labels (meta(Delta_pqr), Sec. 3) -- is folded into exact integer tables, the
+ * GPU-resident counterpart of the user callbacks of Sec. 4.5 (Alg. 2, 3, 4).
+ *
+ * Conventions shared by every entry point:
+ *   - Pointers marked "device or host" may point to device memory or to host
+ *     memory (pageable or pinned); the library detects which and copies host
+ *     data itself.  The caller keeps ownership of every buffer it passes.
+ *   - All GPU work is ordered on the caller's CUDA stream `cuda_stream`
+ *     (a cudaStream_t; NULL = the legacy default stream).  Entry points that
+ *     return graph statistics or write host memory synchronise that stream.
+ *   - Every call returns a tripoll_status.  Arguments are validated before any
+ *     kernel that writes caller memory runs; on failure nothing is left
+ *     allocated and *out handles are not written.
+ *   - All arithmetic is integer; results are bit-exact and independent of the
+ *     schedule.
+ *   - Vertex ids are uint32 in [0, num_vertices); timestamps are uint32;
+ *     labels are uint8 in [0, L).
+ */
+#ifndef TRIPOLL_H
+#define TRIPOLL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tripoll_graph* tripoll_graph_t;
+typedef struct tripoll_server* tripoll_server_t;
+
+typedef enum {
+    TRIPOLL_OK = 0,
+    TRIPOLL_ERR_INVALID_ARG = -1,    /* null handle/pointer, zero label count, t_lo > t_hi, ... */
+    TRIPOLL_ERR_VERTEX_RANGE = -2,   /* an edge endpoint >= num_vertices */
+    TRIPOLL_ERR_LABEL_RANGE = -3,    /* a vertex label >= num_vlabels or edge label >= num_elabels */
+    TRIPOLL_ERR_NO_MEMORY = -4,      /* device allocation failed or a scratch budget would be exceeded */
+    TRIPOLL_ERR_CUDA = -5,           /* a CUDA runtime call failed; see tripoll_last_error() */
+    TRIPOLL_ERR_TIMEOUT = -6,        /* a bounded wait ran out */
+    TRIPOLL_ERR_NO_EDGE_LABELS = -7, /* an edge-label survey on a graph built without edge labels */
+    TRIPOLL_ERR_NOT_FOUND = -8       /* unknown request or graph slot */
+} tripoll_status;
+
+/* Survey kinds (bit mask).  The result buffer holds the requested tables in
+ * this order, each immediately after the previous one (uint64 words):
+ *
+ *   TRIPOLL_COUNT           1 word   number of triangles in the window (Alg. 2).
+ *   TRIPOLL_CLOSURE_HIST   33 words  closing time t3 - t1 of the sorted edge
+ *                                    timestamps t1 <= t2 <= t3, counted in bin
+ *                                    ceil(log2(t3 - t1)); differences 0 and 1
+ *                                    both land in bin 0 (Sec. 5.8, Alg. 4).
+ *   TRIPOLL_VLABEL_TRIPLES Lv^3      sorted vertex-label triple a <= b <= c at
+ *                                    index (a*Lv + b)*Lv + c; other entries 0.
+ *   TRIPOLL_ELABEL_TRIPLES Le^3      the same over the three edge labels.
+ *   TRIPOLL_OPEN_CLOSE_HIST 33*33    joint (open, close) table of Alg. 4 at
+ *                                    index open*33 + close, open = ceil(log2(t2 - t1)).
+ *   TRIPOLL_MAX_ELABEL     Le        Alg. 3: among triangles whose three vertex
+ *                                    labels are pairwise distinct, the count per
+ *                                    maximum edge label.
+ *   TRIPOLL_DEGREE_TRIPLES 33^3      Sec. 5.10: sorted triple of ceil(log2 d(v))
+ *                                    of the three vertices (d = degree in the
+ *                                    simple graph), indexed like the label triples.
+ *   TRIPOLL_VERTEX_LOCAL   n         local triangle participation per vertex, by
+ *                                    input vertex id (Sec. 5.3).
+ *
+ * A triangle is surveyed iff its three edge timestamps all lie in the inclusive
+ * window [t_lo, t_hi]; [0, 0xFFFFFFFF] surveys every triangle.  This equals
+ * surveying the subgraph of the edges whose timestamp lies in the window. */
+enum {
+    TRIPOLL_COUNT = 1,
+    TRIPOLL_CLOSURE_HIST = 2,
+    TRIPOLL_VLABEL_TRIPLES = 4,
+    TRIPOLL_ELABEL_TRIPLES = 8,
+    TRIPOLL_OPEN_CLOSE_HIST = 16,
+    TRIPOLL_MAX_ELABEL = 32,
+    TRIPOLL_DEGREE_TRIPLES = 64,
+    TRIPOLL_VERTEX_LOCAL = 128
+};
+#define TRIPOLL_ALL_KINDS 255u
+#define TRIPOLL_HIST_BINS 33u
+
+/* Statistics of a built graph (G+ of Sec. 3).  Sizes are counts, not bytes. */
+typedef struct {
+    uint64_t num_vertices;   /* n */
+    uint64_t num_input_edges;/* records passed to create */
+    uint64_t num_edges;      /* m = |E+|: unique undirected edges after loop removal and dedup */
+    uint64_t wedges;         /* |W+| = sum_p C(d+(p), 2) (Sec. 3) */
+    uint64_t dplus_max;      /* max_p d+(p) */
+    uint64_t degree_max;     /* max_v d(v) */
+    uint64_t q_list_words;   /* sum over directed edges (p,q) of d+(q): out-list entries read once per in-edge */
+    uint64_t num_graphs;     /* 1, or the number of graphs of a batched build */
+    uint32_t num_vlabels;
+    uint32_t num_elabels;    /* 0 when the graph has no edge labels */
+    uint64_t device_bytes;   /* HBM held by the graph */
+} tripoll_graph_info;
+
+/* Build G+ on the device (Sec. 3, Sec. 4.2): drop records with src == dst; merge
+ * all records of an unordered pair into one edge keeping the lexicographic
+ * minimum (timestamp, then edge label) -- the chronologically first record of
+ * Sec. 5.2; compute degrees of the simple graph; order vertices by
+ * (degree, id) -- the order <+ of Sec. 3 with the vertex id as tie-break;
+ * direct each edge from its <+ -smaller end; store sorted out-lists (CSR) with
+ * timestamp and edge-label arrays aligned to them and vertex labels permuted
+ * to <+ order.
+ *
+ *   src, dst, ts  device or host, uint32[num_edges]: edge records.
+ *   elabel        device or host, uint8[num_edges], or NULL (no edge labels).
+ *   vlabel        device or host, uint8[num_vertices], or NULL (all labels 0).
+ *   num_vlabels   >= 1 (1 when vlabel is NULL); num_elabels >= 1 when elabel != NULL.
+ *   Errors: VERTEX_RANGE / LABEL_RANGE when a record or label is out of range,
+ *   NO_MEMORY, CUDA.  Synchronises cuda_stream. */
+int tripoll_graph_create(const uint32_t* src, const uint32_t* dst, const uint32_t* ts,
+                         const uint8_t* elabel, uint64_t num_edges, const uint8_t* vlabel,
+                         uint32_t num_vertices, uint32_t num_vlabels, uint32_t num_elabels,
+                         void* cuda_stream, tripoll_graph_t* out);
+
+/* Build one G+ holding many independent graphs (the batched workload).  Graph
+ * i owns input records [edge_offsets[i], edge_offsets[i+1]) with vertex ids
+ * local to it in [0, num_vertices[i]), and vertex labels at
+ * vlabel[sum_{j<i} num_vertices[j] + v].  Each graph is built exactly as
+ * tripoll_graph_create would build it alone.
+ *   edge_offsets  host, uint64[num_graphs + 1], edge_offsets[0] == 0.
+ *   num_vertices  host, uint32[num_graphs].
+ * Other arguments as in tripoll_graph_create.  Synchronises cuda_stream. */
+int tripoll_batch_create(const uint32_t* src, const uint32_t* dst, const uint32_t* ts,
+                         const uint8_t* elabel, const uint64_t* edge_offsets,
+                         const uint8_t* vlabel, const uint32_t* num_vertices, uint32_t num_graphs,
+                         uint32_t num_vlabels, uint32_t num_elabels, void* cuda_stream,
+                         tripoll_graph_t* out);
+
+/* Number of uint64 words of a result for kind_mask (TRIPOLL_VERTEX_LOCAL adds
+ * num_vertices words, the others fixed sizes listed above). */
+uint64_t tripoll_result_words(uint32_t kind_mask, uint32_t num_vlabels, uint32_t num_elabels,
+                              uint64_t num_vertices);
+
+/* Run one survey (Alg. 1 with the fold of the requested kinds) over every
+ * triangle of g whose edge timestamps lie in [t_lo, t_hi].
+ *   result  device or host, uint64[tripoll_result_words(kinds, ...)]; overwritten.
+ *           For a batched graph: uint64[num_graphs * words], graph i's tables
+ *           at offset i * words.
+ *   Errors: INVALID_ARG (t_lo > t_hi, kind_mask == 0 or unknown bits),
+ *   NO_EDGE_LABELS, NO_MEMORY, CUDA.  Asynchronous for a device result;
+ *   synchronises cuda_stream for a host result. */
+int tripoll_survey(tripoll_graph_t g, uint32_t kind_mask, uint32_t t_lo, uint32_t t_hi,
+                   uint64_t* result, void* cuda_stream);
+
+/* The same survey restricted to the pivots p (the <+ -smallest vertex of each
+ * triangle, Sec. 3) at positions [pivot_lo, pivot_hi) of the <+ order.  The
+ * sum of the results over a partition of [0, n) equals tripoll_survey's
+ * result: this is the unit a multi-GPU run shards (each rank one range, then
+ * one elementwise sum, the all_reduce of Alg. 2). */
+int tripoll_survey_range(tripoll_graph_t g, uint32_t kind_mask, uint32_t t_lo, uint32_t t_hi,
+                         uint64_t pivot_lo, uint64_t pivot_hi, uint64_t* result,
+                         void* cuda_stream);
+
+/* Split [0, n) into `parts` pivot ranges of near-equal survey cost (the
+ * out-list entries each pivot's wedge checks read).  bounds: host,
+ * uint64[parts + 1], bounds[0] = 0, bounds[parts] = n.  Synchronises. */
+int tripoll_partition_pivots(tripoll_graph_t g, uint32_t parts, uint64_t* bounds,
+                             void* cuda_stream);
+
+/* Statistics of g.  Host output. */
+int tripoll_graph_stats(tripoll_graph_t g, tripoll_graph_info* info);
+
+/* Copy out the built G+ (for checking the builder): any pointer may be NULL.
+ *   offsets  uint64[n+1], col uint32[m] (targets as positions in <+), ts
+ *   uint32[m], elabel uint8[m], order uint32[n] (input id at each position).
+ *   All host pointers.  Synchronises cuda_stream. */
+int tripoll_graph_export(tripoll_graph_t g, uint64_t* offsets, uint32_t* col, uint32_t* ts,
+                         uint8_t* elabel, uint32_t* order, void* cuda_stream);
+
+/* Release the graph's device memory.  The caller must not destroy a graph
+ * while surveys on it may still run on some stream. */
+void tripoll_destroy(tripoll_graph_t g);
+
+/* ---- serving: resident graphs, continuous batching of survey requests ----
+ *
+ * A server owns a dispatcher thread and a set of CUDA streams.  Requests
+ * (graph slot, kinds, window) are admitted while their result and scratch
+ * memory fit under scratch_cap_bytes and fewer than max_inflight requests are
+ * on the device; admitted requests are launched together (one launch per
+ * admission round, several rounds in flight on different streams), and every
+ * request that arrives meanwhile joins the next round.  Results are the same
+ * as tripoll_survey's for that request alone. */
+int tripoll_server_create(uint64_t scratch_cap_bytes, uint32_t max_inflight,
+                          tripoll_server_t* out);
+/* Make g resident in the server (the server does not take ownership). */
+int tripoll_server_add_graph(tripoll_server_t s, tripoll_graph_t g, uint32_t* slot);
+/* Queue a request; returns its id.  Thread-safe. */
+int tripoll_server_submit(tripoll_server_t s, uint32_t slot, uint32_t kind_mask, uint32_t t_lo,
+                          uint32_t t_hi, uint64_t* request_id);
+/* Wait up to timeout_ms for a request; on success copy its result (host,
+ * uint64[words]) and its latency in nanoseconds (submit to result on host).
+ * TIMEOUT when it is not done in time (it stays queued). */
+int tripoll_server_wait(tripoll_server_t s, uint64_t request_id, uint64_t* result,
+                        uint64_t* latency_ns, uint32_t timeout_ms);
+void tripoll_server_destroy(tripoll_server_t s);
+
+/* Number of the library's own kernels launched by this process so far (not
+ * counting launches made inside CUB routines).  For launch accounting only. */
+uint64_t tripoll_launch_count(void);
+
+/* Human-readable text of a status, and the detail of the calling thread's
+ * last error (static storage; never NULL). */
+const char* tripoll_status_string(int status);
+const char* tripoll_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TRIPOLL_H */

@@ -142,8 +142,9 @@ typedef struct {
     const adj_t* adj;
     const uint32_t* vertex_at; /* input id at each position */
     uint32_t t_lo, t_hi;
-    /* work */
+    /* work: the pivot positions in [p_lo, p_hi) whose block of 256 is t mod stride */
     uint32_t p_lo, p_hi;
+    uint32_t t, stride;
     /* outputs (private per thread) */
     oracle_out out;
 } work_t;
@@ -198,10 +199,11 @@ static void fold(const work_t* w, uint32_t p, uint32_t q, uint32_t r, uint64_t e
     }
 }
 
-/* Step 5 for the pivots at positions [p_lo, p_hi). */
+/* Step 5 for this thread's pivots of [p_lo, p_hi). */
 static void* survey_pivots(void* arg) {
     work_t* w = (work_t*)arg;
     for (uint32_t pp = w->p_lo; pp < w->p_hi; ++pp) {
+        if (((pp - w->p_lo) >> 8) % w->stride != w->t) continue;
         const uint32_t p = w->vertex_at[pp];
         const adj_t* P = w->adj + w->adj_start[pp];
         const uint64_t dp = w->adj_start[pp + 1] - w->adj_start[pp];
@@ -338,7 +340,7 @@ int oracle_survey(const uint32_t* src, const uint32_t* dst, const uint32_t* ts, 
         stats->dmax = dmax;
     }
 
-    /* 5 + 6: pivots split into `threads` contiguous blocks with private outputs */
+    /* 5 + 6: pivots dealt to `threads` workers in interleaved blocks of 256, private outputs */
     const uint64_t lv3 = (uint64_t)Lv * Lv * Lv, le3 = (uint64_t)Le * Le * Le;
     const uint64_t dt3 = (uint64_t)HIST_BINS * HIST_BINS * HIST_BINS;
     work_t* works = (work_t*)calloc((size_t)threads, sizeof(work_t));
@@ -352,8 +354,10 @@ int oracle_survey(const uint32_t* src, const uint32_t* dst, const uint32_t* ts, 
         w->ets = ets; w->eel = el ? eel : NULL; w->vl = vl;
         w->deg = deg; w->adj_start = adj_start; w->adj = adj; w->vertex_at = vertex_at;
         w->t_lo = t_lo; w->t_hi = t_hi;
-        w->p_lo = lo + (uint32_t)(((uint64_t)(pivot_hi - lo) * t) / threads);
-        w->p_hi = lo + (uint32_t)(((uint64_t)(pivot_hi - lo) * (t + 1)) / threads);
+        w->p_lo = lo;
+        w->p_hi = pivot_hi;
+        w->t = (uint32_t)t;
+        w->stride = (uint32_t)threads;
         if (t == 0) {
             w->out = *out; /* thread 0 accumulates straight into the caller's arrays */
         } else {

@@ -1,0 +1,194 @@
+// abi.cu -- the C entry points around the builder and the survey kernels:
+// status text, argument checks, result buffers, statistics, export, shards.
+#include <cub/cub.cuh>
+
+#include <algorithm>
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace tp {
+
+namespace {
+thread_local std::string g_last_error;
+std::atomic<uint64_t> g_launches{0};
+}
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+int fail(int status, const std::string& msg) {
+    g_last_error = msg;
+    return status;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? TRIPOLL_ERR_NO_MEMORY : TRIPOLL_ERR_CUDA;
+}
+
+bool is_device_pointer(const void* p) {
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+int check_survey_args(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_t t_hi, const void* result) {
+    if (!g) return fail(TRIPOLL_ERR_INVALID_ARG, "graph handle is NULL");
+    if (!result) return fail(TRIPOLL_ERR_INVALID_ARG, "result is NULL");
+    if (kinds == 0 || (kinds & ~TRIPOLL_ALL_KINDS)) return fail(TRIPOLL_ERR_INVALID_ARG, "bad kind mask");
+    if (t_lo > t_hi) return fail(TRIPOLL_ERR_INVALID_ARG, "t_lo > t_hi");
+    if ((kinds & (TRIPOLL_ELABEL_TRIPLES | TRIPOLL_MAX_ELABEL)) && !g->has_el)
+        return fail(TRIPOLL_ERR_NO_EDGE_LABELS, "edge-label survey on a graph without edge labels");
+    if ((kinds & TRIPOLL_VERTEX_LOCAL) && g->graph_of)
+        return fail(TRIPOLL_ERR_INVALID_ARG, "local counts are not available for batched graphs");
+    return TRIPOLL_OK;
+}
+
+// Survey into `result` (device or host), pivots [p_lo, p_hi).
+int survey_into(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_t t_hi, uint64_t p_lo, uint64_t p_hi,
+                uint64_t* result, cudaStream_t s) {
+    int rc = check_survey_args(g, kinds, t_lo, t_hi, result);
+    if (rc) return rc;
+    const Layout lay = make_layout(kinds, g->Lv, g->Le, g->n);
+    const uint64_t words = lay.words * g->num_graphs;
+    const bool dev_result = is_device_pointer(result);
+    Scratch acc, ctr;
+    TP_CUDA(ctr.alloc(16, s));
+    unsigned long long* a = reinterpret_cast<unsigned long long*>(result);
+    if (!dev_result) {
+        TP_CUDA(acc.alloc(words * 8, s));
+        a = acc.as<unsigned long long>();
+    }
+    TP_CUDA(cudaMemsetAsync(a, 0, words * 8, s));
+    if (p_hi > g->n) p_hi = g->n;
+    if (p_lo < p_hi && (rc = launch_survey(g, kinds, t_lo, t_hi, p_lo, p_hi, a, ctr.as<uint32_t>(), s)))
+        return rc;
+    if (!dev_result) {
+        TP_CUDA(cudaMemcpyAsync(result, a, words * 8, cudaMemcpyDeviceToHost, s));
+        TP_CUDA(cudaStreamSynchronize(s));
+    }
+    return TRIPOLL_OK;
+}
+
+namespace {
+
+// survey cost of each pivot position: the wedges rooted at it plus its out-edges
+__global__ void pivot_cost_kernel(const uint64_t* __restrict__ off, uint64_t n, uint64_t* __restrict__ cost) {
+    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < n; p += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t d = off[p + 1] - off[p];
+        cost[p] = d * (d ? d - 1 : 0) / 2 + d;
+    }
+}
+
+// bounds[i] = first position whose inclusive prefix cost exceeds total*i/parts
+__global__ void cut_kernel(const uint64_t* __restrict__ prefix, uint64_t n, uint32_t parts, uint64_t* bounds) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > parts) return;
+    if (i == 0) { bounds[0] = 0; return; }
+    if (i == parts) { bounds[parts] = n; return; }
+    const uint64_t total = n ? prefix[n - 1] : 0;
+    const unsigned __int128 target128 = (unsigned __int128)total * i / parts;
+    const uint64_t target = (uint64_t)target128;
+    uint64_t lo = 0, hi = n;
+    while (lo < hi) {
+        uint64_t mid = lo + ((hi - lo) >> 1);
+        if (prefix[mid] <= target) lo = mid + 1; else hi = mid;
+    }
+    bounds[i] = lo;
+}
+
+}  // namespace
+}  // namespace tp
+
+using namespace tp;
+
+extern "C" const char* tripoll_status_string(int status) {
+    switch (status) {
+        case TRIPOLL_OK: return "ok";
+        case TRIPOLL_ERR_INVALID_ARG: return "invalid argument";
+        case TRIPOLL_ERR_VERTEX_RANGE: return "vertex id out of range";
+        case TRIPOLL_ERR_LABEL_RANGE: return "label out of range";
+        case TRIPOLL_ERR_NO_MEMORY: return "out of device memory or scratch budget";
+        case TRIPOLL_ERR_CUDA: return "CUDA error";
+        case TRIPOLL_ERR_TIMEOUT: return "timed out";
+        case TRIPOLL_ERR_NO_EDGE_LABELS: return "graph has no edge labels";
+        case TRIPOLL_ERR_NOT_FOUND: return "not found";
+        default: return "unknown status";
+    }
+}
+
+extern "C" const char* tripoll_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" uint64_t tripoll_launch_count(void) { return g_launches.load(); }
+
+extern "C" uint64_t tripoll_result_words(uint32_t kind_mask, uint32_t num_vlabels, uint32_t num_elabels,
+                                         uint64_t num_vertices) {
+    return make_layout(kind_mask, num_vlabels ? num_vlabels : 1, num_elabels ? num_elabels : 1, num_vertices).words;
+}
+
+extern "C" int tripoll_survey(tripoll_graph_t g, uint32_t kind_mask, uint32_t t_lo, uint32_t t_hi, uint64_t* result,
+                              void* cuda_stream) {
+    return survey_into(g, kind_mask, t_lo, t_hi, 0, g ? g->n : 0, result, (cudaStream_t)cuda_stream);
+}
+
+extern "C" int tripoll_survey_range(tripoll_graph_t g, uint32_t kind_mask, uint32_t t_lo, uint32_t t_hi,
+                                    uint64_t pivot_lo, uint64_t pivot_hi, uint64_t* result, void* cuda_stream) {
+    if (pivot_lo > pivot_hi) return fail(TRIPOLL_ERR_INVALID_ARG, "pivot_lo > pivot_hi");
+    return survey_into(g, kind_mask, t_lo, t_hi, pivot_lo, pivot_hi, result, (cudaStream_t)cuda_stream);
+}
+
+extern "C" int tripoll_partition_pivots(tripoll_graph_t g, uint32_t parts, uint64_t* bounds, void* cuda_stream) {
+    if (!g || !bounds || parts == 0) return fail(TRIPOLL_ERR_INVALID_ARG, "bad partition arguments");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const uint64_t n = g->n;
+    Scratch cost, prefix, tmp, cuts;
+    TP_CUDA(cost.alloc((n + 1) * 8, s));
+    TP_CUDA(prefix.alloc((n + 1) * 8, s));
+    TP_CUDA(cuts.alloc((parts + 1) * 8ull, s));
+    if (n) {
+        pivot_cost_kernel<<<(unsigned)std::min<uint64_t>((n + 255) / 256, 148 * 64), 256, 0, s>>>(g->off, n,
+                                                                                               cost.as<uint64_t>()); ::tp::note_launch();
+        size_t tb = 0;
+        TP_CUDA(cub::DeviceScan::InclusiveSum(nullptr, tb, cost.as<uint64_t>(), prefix.as<uint64_t>(), n, s));
+        TP_CUDA(tmp.alloc(tb, s));
+        TP_CUDA(cub::DeviceScan::InclusiveSum(tmp.ptr, tb, cost.as<uint64_t>(), prefix.as<uint64_t>(), n, s));
+    }
+    cut_kernel<<<(parts + 1 + 255) / 256, 256, 0, s>>>(prefix.as<uint64_t>(), n, parts, cuts.as<uint64_t>()); ::tp::note_launch();
+    TP_CUDA(cudaGetLastError());
+    TP_CUDA(cudaMemcpyAsync(bounds, cuts.ptr, (parts + 1) * 8ull, cudaMemcpyDeviceToHost, s));
+    TP_CUDA(cudaStreamSynchronize(s));
+    return TRIPOLL_OK;
+}
+
+extern "C" int tripoll_graph_stats(tripoll_graph_t g, tripoll_graph_info* info) {
+    if (!g || !info) return fail(TRIPOLL_ERR_INVALID_ARG, "NULL argument");
+    *info = g->info;
+    return TRIPOLL_OK;
+}
+
+extern "C" int tripoll_graph_export(tripoll_graph_t g, uint64_t* offsets, uint32_t* col, uint32_t* ts,
+                                    uint8_t* elabel, uint32_t* order, void* cuda_stream) {
+    if (!g) return fail(TRIPOLL_ERR_INVALID_ARG, "graph handle is NULL");
+    if (elabel && !g->has_el) return fail(TRIPOLL_ERR_NO_EDGE_LABELS, "graph has no edge labels");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (offsets) TP_CUDA(cudaMemcpyAsync(offsets, g->off, (g->n + 1) * 8, cudaMemcpyDeviceToHost, s));
+    if (col && g->m) TP_CUDA(cudaMemcpyAsync(col, g->col, g->m * 4, cudaMemcpyDeviceToHost, s));
+    if (ts && g->m) TP_CUDA(cudaMemcpyAsync(ts, g->ts, g->m * 4, cudaMemcpyDeviceToHost, s));
+    if (elabel && g->m) TP_CUDA(cudaMemcpyAsync(elabel, g->el, g->m, cudaMemcpyDeviceToHost, s));
+    if (order && g->n) TP_CUDA(cudaMemcpyAsync(order, g->order, g->n * 4, cudaMemcpyDeviceToHost, s));
+    TP_CUDA(cudaStreamSynchronize(s));
+    return TRIPOLL_OK;
+}
+
+extern "C" void tripoll_destroy(tripoll_graph_t g) {
+    if (!g) return;
+    free_graph_arrays(g);
+    delete g;
+}

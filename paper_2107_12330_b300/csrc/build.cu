@@ -1,0 +1,566 @@
+// build.cu -- on-device construction of G+ (TriPoll Sec. 3 and Sec. 4.2).
+//
+// Steps, all on the caller's stream:
+//   validate   ids < n (per graph when batched), labels < L
+//   canon      (u,v) -> key (min,max) packed in 2b bits, loops -> sentinel key;
+//              payload (ts << 8 | elabel)
+//   sort       radix sort of (key, payload) pairs
+//   dedup      min payload per key run: the chronologically first record of
+//              each unordered pair (Sec. 5.2), edge label as tie-break
+//   degree     d(v) of the simple graph
+//   order      vertices sorted by (graph, degree, id): the order <+ of Sec. 3
+//              with the id as tie-break, per graph when batched
+//   orient     every edge directed from the <+ -smaller end; sorted by
+//              (source position, target position): the out-lists Adj+ (CSR)
+//              with timestamps and edge labels aligned to them (Adj+^m)
+//   in-edges   the same edges sorted by (target, source): for every middle
+//              vertex q the directed edges (p,q) that end at it
+//   stats      |E+|, |W+| = sum C(d+,2), d+ max, ...
+#include <cub/cub.cuh>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+
+namespace tp {
+namespace {
+
+constexpr int kThreads = 256;
+
+unsigned grid_for(uint64_t items, unsigned cap = 148u * 64u) {
+    uint64_t b = (items + kThreads - 1) / kThreads;
+    if (b < 1) b = 1;
+    return (unsigned)std::min<uint64_t>(b, cap);
+}
+
+int bits_for(uint64_t x) {  // bits to hold values 0..x
+    int b = 1;
+    while (b < 64 && (x >> b) != 0) ++b;
+    return b;
+}
+
+__device__ __forceinline__ uint32_t graph_of_edge(const uint64_t* eoff, uint32_t G, uint64_t i) {
+    // largest g with eoff[g] <= i
+    uint32_t lo = 0, hi = G - 1;
+    while (lo < hi) {
+        uint32_t mid = (lo + hi + 1) >> 1;
+        if (eoff[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void validate_edges_kernel(const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst,
+                                      const uint8_t* __restrict__ el, uint64_t m, uint32_t n,
+                                      const uint64_t* __restrict__ eoff, const uint32_t* __restrict__ nv,
+                                      uint32_t G, uint32_t Le, unsigned* flags) {
+    unsigned f = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t lim = n;
+        if (eoff) lim = nv[graph_of_edge(eoff, G, i)];
+        if (src[i] >= lim || dst[i] >= lim) f |= 1u;
+        if (el && el[i] >= Le) f |= 2u;
+    }
+    if (f) atomicOr(flags, f);
+}
+
+__global__ void validate_vl_kernel(const uint8_t* __restrict__ vl, uint64_t n, uint32_t Lv, unsigned* flags) {
+    unsigned f = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        if (vl[i] >= Lv) f |= 4u;
+    if (f) atomicOr(flags, f);
+}
+
+__global__ void canon_kernel(const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst,
+                             const uint32_t* __restrict__ ts, const uint8_t* __restrict__ el, uint64_t m,
+                             const uint64_t* __restrict__ eoff, const uint64_t* __restrict__ vbase, uint32_t G,
+                             int b, uint64_t sentinel, uint64_t* __restrict__ key, uint64_t* __restrict__ val) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t u = src[i], v = dst[i];
+        if (eoff) {
+            uint64_t base = vbase[graph_of_edge(eoff, G, i)];
+            u += base;
+            v += base;
+        }
+        uint64_t lo = u < v ? u : v, hi = u < v ? v : u;
+        key[i] = (u == v) ? sentinel : ((lo << b) | hi);
+        val[i] = ((uint64_t)ts[i] << 8) | (el ? el[i] : 0u);
+    }
+}
+
+struct MinOp {
+    __device__ __forceinline__ uint64_t operator()(uint64_t a, uint64_t b) const { return a < b ? a : b; }
+};
+
+__global__ void unique_count_kernel(const uint64_t* ukey, const uint64_t* runs, uint64_t sentinel, uint64_t* m_out) {
+    uint64_t r = *runs;
+    if (r > 0 && ukey[r - 1] == sentinel) r -= 1;
+    *m_out = r;
+}
+
+__global__ void degree_kernel(const uint64_t* __restrict__ ukey, uint64_t m, int b, uint32_t* __restrict__ deg) {
+    const uint64_t mask = (1ull << b) - 1;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t k = ukey[i];
+        atomicAdd(&deg[k >> b], 1u);
+        atomicAdd(&deg[k & mask], 1u);
+    }
+}
+
+__global__ void max_u32_kernel(const uint32_t* __restrict__ x, uint64_t n, unsigned* out) {
+    unsigned mx = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        mx = max(mx, x[i]);
+    for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0 && mx) atomicMax(out, mx);
+}
+
+__global__ void vertex_key_kernel(const uint32_t* __restrict__ deg, uint64_t n, const uint64_t* __restrict__ vbase,
+                                  uint32_t G, int b, int bd, uint64_t* __restrict__ vkey) {
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
+         v += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t g = 0;
+        if (vbase) {  // largest g with vbase[g] <= v
+            uint32_t lo = 0, hi = G - 1;
+            while (lo < hi) {
+                uint32_t mid = (lo + hi + 1) >> 1;
+                if (vbase[mid] <= v) lo = mid; else hi = mid - 1;
+            }
+            g = lo;
+        }
+        vkey[v] = (g << (bd + b)) | ((uint64_t)deg[v] << b) | v;
+    }
+}
+
+__global__ void rank_kernel(const uint64_t* __restrict__ vkey, uint64_t n, int b, uint32_t* __restrict__ rank,
+                            uint32_t* __restrict__ order, const uint32_t* __restrict__ deg,
+                            uint32_t* __restrict__ deg_pos, int gshift, uint32_t* __restrict__ graph_of) {
+    const uint64_t mask = (1ull << b) - 1;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t k = vkey[i];
+        uint32_t v = (uint32_t)(k & mask);
+        rank[v] = (uint32_t)i;
+        order[i] = v;
+        deg_pos[i] = deg[v];
+        if (graph_of) graph_of[i] = (uint32_t)(k >> gshift);
+    }
+}
+
+__global__ void orient_kernel(const uint64_t* __restrict__ ukey, uint64_t m, int b, const uint32_t* __restrict__ rank,
+                              uint64_t* __restrict__ okey, uint32_t* __restrict__ dplus) {
+    const uint64_t mask = (1ull << b) - 1;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t k = ukey[i];
+        uint64_t ru = rank[k >> b], rv = rank[k & mask];
+        uint64_t s = ru < rv ? ru : rv, d = ru < rv ? rv : ru;
+        okey[i] = (s << b) | d;
+        atomicAdd(&dplus[s], 1u);
+    }
+}
+
+__global__ void csr_fill_kernel(const uint64_t* __restrict__ okey, const uint64_t* __restrict__ oval, uint64_t m,
+                                int b, uint32_t* __restrict__ col, uint32_t* __restrict__ ts, uint8_t* __restrict__ el,
+                                uint64_t* __restrict__ ckey, uint32_t* __restrict__ cval, uint32_t* __restrict__ din) {
+    const uint64_t mask = (1ull << b) - 1;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t k = okey[i], v = oval[i];
+        uint64_t s = k >> b, d = k & mask;
+        col[i] = (uint32_t)d;
+        ts[i] = (uint32_t)(v >> 8);
+        if (el) el[i] = (uint8_t)(v & 0xffu);
+        ckey[i] = (d << b) | s;
+        cval[i] = (uint32_t)i;
+        atomicAdd(&din[d], 1u);
+    }
+}
+
+__global__ void in_edge_fill_kernel(const uint64_t* __restrict__ ckey, const uint32_t* __restrict__ cval, uint64_t m,
+                                    int b, const uint64_t* __restrict__ off, InEdge* __restrict__ in_edge) {
+    const uint64_t mask = (1ull << b) - 1;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t p = (uint32_t)(ckey[i] & mask);
+        InEdge ie;
+        ie.e = cval[i];
+        ie.end = (uint32_t)off[p + 1];
+        ie.p = p;
+        ie.pad = 0;
+        in_edge[i] = ie;
+    }
+}
+
+__global__ void vlabel_pos_kernel(const uint8_t* __restrict__ vl, const uint32_t* __restrict__ order, uint64_t n,
+                                  uint8_t* __restrict__ vl_pos) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        vl_pos[i] = vl ? vl[order[i]] : 0;
+}
+
+// stats[0] = wedges, [1] = q_list_words, [2] = dplus_max, [3] = degree_max
+__global__ void stats_kernel(const uint64_t* __restrict__ off, const uint64_t* __restrict__ in_off,
+                             const uint32_t* __restrict__ deg, uint64_t n, unsigned long long* stats) {
+    unsigned long long w = 0, ql = 0, dm = 0, gm = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t dp = off[i + 1] - off[i];
+        uint64_t di = in_off[i + 1] - in_off[i];
+        w += dp * (dp ? dp - 1 : 0) / 2;
+        ql += dp * di;
+        dm = max(dm, (unsigned long long)dp);
+        gm = max(gm, (unsigned long long)deg[i]);
+    }
+    for (int o = 16; o; o >>= 1) {
+        w += __shfl_xor_sync(0xffffffffu, w, o);
+        ql += __shfl_xor_sync(0xffffffffu, ql, o);
+        dm = max(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+        gm = max(gm, __shfl_xor_sync(0xffffffffu, gm, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (w) atomicAdd(&stats[0], w);
+        if (ql) atomicAdd(&stats[1], ql);
+        if (dm) atomicMax(&stats[2], dm);
+        if (gm) atomicMax(&stats[3], gm);
+    }
+}
+
+// Device copy of a caller array that may live in host memory.
+struct Input {
+    const void* dptr = nullptr;
+    Scratch copy;
+    int bind(const void* p, size_t bytes, cudaStream_t s) {
+        if (!p) { dptr = nullptr; return TRIPOLL_OK; }
+        if (is_device_pointer(p)) { dptr = p; return TRIPOLL_OK; }
+        TP_CUDA(copy.alloc(bytes, s));
+        TP_CUDA(cudaMemcpyAsync(copy.ptr, p, bytes, cudaMemcpyHostToDevice, s));
+        dptr = copy.ptr;
+        return TRIPOLL_OK;
+    }
+};
+
+template <class T> cudaError_t dalloc(T** p, uint64_t count) {
+    return cudaMalloc((void**)p, std::max<uint64_t>(count, 1) * sizeof(T));
+}
+
+struct GraphGuard {  // frees a half-built graph on any error path
+    tripoll_graph* g;
+    explicit GraphGuard(tripoll_graph* g_) : g(g_) {}
+    ~GraphGuard() {
+        if (g) { free_graph_arrays(g); delete g; }
+    }
+    tripoll_graph* release() { tripoll_graph* r = g; g = nullptr; return r; }
+};
+
+int build_impl(const uint32_t* src_h, const uint32_t* dst_h, const uint32_t* ts_h, const uint8_t* el_h,
+               uint64_t m_in, const uint8_t* vl_h, uint64_t n, uint32_t Lv, uint32_t Le,
+               const uint64_t* edge_offsets, const uint32_t* num_vertices, uint32_t G,
+               cudaStream_t s, tripoll_graph_t* out) {
+    if (!out) return fail(TRIPOLL_ERR_INVALID_ARG, "out handle is NULL");
+    if (m_in > 0 && (!src_h || !dst_h || !ts_h)) return fail(TRIPOLL_ERR_INVALID_ARG, "src/dst/ts NULL");
+    if (Lv == 0 || Lv > 256) return fail(TRIPOLL_ERR_INVALID_ARG, "num_vlabels must be in 1..256");
+    if (el_h && (Le == 0 || Le > 256)) return fail(TRIPOLL_ERR_INVALID_ARG, "num_elabels must be in 1..256");
+    if (n > 0xFFFFFFFFull) return fail(TRIPOLL_ERR_INVALID_ARG, "too many vertices for 32-bit ids");
+    if (m_in >= (1ull << 40)) return fail(TRIPOLL_ERR_INVALID_ARG, "too many edge records");
+    const bool batched = edge_offsets != nullptr;
+
+    int dev = 0;
+    TP_CUDA(cudaGetDevice(&dev));
+    Input src, dst, ts, el, vl;
+    int rc;
+    if ((rc = src.bind(src_h, m_in * 4, s)) || (rc = dst.bind(dst_h, m_in * 4, s)) ||
+        (rc = ts.bind(ts_h, m_in * 4, s)) || (rc = el.bind(el_h, m_in, s)) || (rc = vl.bind(vl_h, n, s)))
+        return rc;
+
+    // batched: per-graph edge offsets and vertex bases on the device
+    std::vector<uint64_t> vbase_h;
+    Scratch eoff_d, nv_d, vbase_d;
+    if (batched) {
+        vbase_h.resize(G + 1);
+        vbase_h[0] = 0;
+        for (uint32_t i = 0; i < G; ++i) vbase_h[i + 1] = vbase_h[i] + num_vertices[i];
+        TP_CUDA(eoff_d.alloc((G + 1) * 8ull, s));
+        TP_CUDA(nv_d.alloc(G * 4ull, s));
+        TP_CUDA(vbase_d.alloc((G + 1) * 8ull, s));
+        TP_CUDA(cudaMemcpyAsync(eoff_d.ptr, edge_offsets, (G + 1) * 8ull, cudaMemcpyHostToDevice, s));
+        TP_CUDA(cudaMemcpyAsync(nv_d.ptr, num_vertices, G * 4ull, cudaMemcpyHostToDevice, s));
+        TP_CUDA(cudaMemcpyAsync(vbase_d.ptr, vbase_h.data(), (G + 1) * 8ull, cudaMemcpyHostToDevice, s));
+    }
+    const uint64_t* eoff = batched ? eoff_d.as<uint64_t>() : nullptr;
+    const uint64_t* vbase = batched ? vbase_d.as<uint64_t>() : nullptr;
+
+    // 1. validate
+    Scratch flags_d;
+    TP_CUDA(flags_d.alloc(64, s));
+    TP_CUDA(cudaMemsetAsync(flags_d.ptr, 0, 64, s));
+    if (m_in)
+        validate_edges_kernel<<<grid_for(m_in), kThreads, 0, s>>>(
+            (const uint32_t*)src.dptr, (const uint32_t*)dst.dptr, (const uint8_t*)el.dptr, m_in, (uint32_t)n,
+            eoff, nv_d.as<uint32_t>(), G, Le, flags_d.as<unsigned>()); ::tp::note_launch();
+    if (vl.dptr && n)
+        validate_vl_kernel<<<grid_for(n), kThreads, 0, s>>>((const uint8_t*)vl.dptr, n, Lv, flags_d.as<unsigned>()); ::tp::note_launch();
+    TP_CUDA(cudaGetLastError());
+    unsigned flags = 0;
+    TP_CUDA(cudaMemcpyAsync(&flags, flags_d.ptr, 4, cudaMemcpyDeviceToHost, s));
+    TP_CUDA(cudaStreamSynchronize(s));
+    if (flags & 1u) return fail(TRIPOLL_ERR_VERTEX_RANGE, "an edge endpoint is >= the vertex count");
+    if (flags & 6u) return fail(TRIPOLL_ERR_LABEL_RANGE, "a label is >= its label count");
+
+    const int b = bits_for(n ? n - 1 : 0);
+    const uint64_t vmask = (1ull << b) - 1;
+    const uint64_t sentinel = (2 * b >= 64) ? ~0ull : ((1ull << (2 * b)) - 1);
+
+    tripoll_graph* g = new tripoll_graph();
+    GraphGuard guard(g);
+    g->device = dev;
+    g->n = n;
+    g->m_in = m_in;
+    g->num_graphs = batched ? G : 1;
+    g->Lv = Lv;
+    g->Le = el_h ? Le : 1;
+    g->has_el = el_h != nullptr;
+
+    // 2. canonical keys + payloads, sort, keep min payload per key run
+    uint64_t m = 0;
+    Scratch ukey_d, uval_d;
+    {
+        Scratch k0, k1, v0, v1, tmp, runs;
+        TP_CUDA(k0.alloc(m_in * 8, s));
+        TP_CUDA(k1.alloc(m_in * 8, s));
+        TP_CUDA(v0.alloc(m_in * 8, s));
+        TP_CUDA(v1.alloc(m_in * 8, s));
+        if (m_in)
+            canon_kernel<<<grid_for(m_in), kThreads, 0, s>>>(
+                (const uint32_t*)src.dptr, (const uint32_t*)dst.dptr, (const uint32_t*)ts.dptr,
+                (const uint8_t*)el.dptr, m_in, eoff, vbase, G, b, sentinel, k0.as<uint64_t>(), v0.as<uint64_t>()); ::tp::note_launch();
+        TP_CUDA(cudaGetLastError());
+        src.copy.release(); dst.copy.release(); ts.copy.release(); el.copy.release();
+        cub::DoubleBuffer<uint64_t> kb(k0.as<uint64_t>(), k1.as<uint64_t>());
+        cub::DoubleBuffer<uint64_t> vb(v0.as<uint64_t>(), v1.as<uint64_t>());
+        size_t tb = 0;
+        const int end_bit = std::min(64, 2 * b);
+        TP_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tb, kb, vb, m_in, 0, end_bit, s));
+        TP_CUDA(tmp.alloc(tb, s));
+        TP_CUDA(cub::DeviceRadixSort::SortPairs(tmp.ptr, tb, kb, vb, m_in, 0, end_bit, s));
+        // reduce-by-key into the buffers not holding the sorted data
+        uint64_t* ukey = kb.Alternate();
+        uint64_t* uval = vb.Alternate();
+        TP_CUDA(runs.alloc(16, s));
+        size_t tb2 = 0;
+        TP_CUDA(cub::DeviceReduce::ReduceByKey(nullptr, tb2, kb.Current(), ukey, vb.Current(), uval,
+                                               runs.as<uint64_t>(), MinOp(), m_in, s));
+        if (tb2 > tb) TP_CUDA(tmp.alloc(tb2, s));
+        TP_CUDA(cub::DeviceReduce::ReduceByKey(tmp.ptr, tb2, kb.Current(), ukey, vb.Current(), uval,
+                                               runs.as<uint64_t>(), MinOp(), m_in, s));
+        if (m_in == 0) TP_CUDA(cudaMemsetAsync(runs.ptr, 0, 8, s));
+        unique_count_kernel<<<1, 1, 0, s>>>(ukey, runs.as<uint64_t>(), sentinel, runs.as<uint64_t>() + 1); ::tp::note_launch();
+        TP_CUDA(cudaGetLastError());
+        TP_CUDA(cudaMemcpyAsync(&m, runs.as<uint64_t>() + 1, 8, cudaMemcpyDeviceToHost, s));
+        TP_CUDA(cudaStreamSynchronize(s));
+        if (m >= 0xFFFFFFFFull) return fail(TRIPOLL_ERR_INVALID_ARG, "more than 2^32-2 unique edges");
+        // keep the unique arrays, drop the rest
+        TP_CUDA(ukey_d.alloc(m * 8, s));
+        TP_CUDA(uval_d.alloc(m * 8, s));
+        TP_CUDA(cudaMemcpyAsync(ukey_d.ptr, ukey, m * 8, cudaMemcpyDeviceToDevice, s));
+        TP_CUDA(cudaMemcpyAsync(uval_d.ptr, uval, m * 8, cudaMemcpyDeviceToDevice, s));
+    }
+    g->m = m;
+
+    // 3. degrees
+    Scratch deg_d;
+    TP_CUDA(deg_d.alloc((n + 1) * 4, s));
+    TP_CUDA(cudaMemsetAsync(deg_d.ptr, 0, (n + 1) * 4, s));
+    if (m) degree_kernel<<<grid_for(m), kThreads, 0, s>>>(ukey_d.as<uint64_t>(), m, b, deg_d.as<uint32_t>()); ::tp::note_launch();
+    TP_CUDA(cudaGetLastError());
+    unsigned dmax = 0;
+    {
+        Scratch mx;
+        TP_CUDA(mx.alloc(4, s));
+        TP_CUDA(cudaMemsetAsync(mx.ptr, 0, 4, s));
+        if (n) max_u32_kernel<<<grid_for(n), kThreads, 0, s>>>(deg_d.as<uint32_t>(), n, mx.as<unsigned>()); ::tp::note_launch();
+        TP_CUDA(cudaGetLastError());
+        TP_CUDA(cudaMemcpyAsync(&dmax, mx.ptr, 4, cudaMemcpyDeviceToHost, s));
+        TP_CUDA(cudaStreamSynchronize(s));
+    }
+
+    // 4. the order <+ : sort vertices by (graph, degree, id)
+    const int bd = bits_for(dmax);
+    const int gb = batched ? bits_for(G ? G - 1 : 0) : 0;
+    if (gb + bd + b > 64) return fail(TRIPOLL_ERR_INVALID_ARG, "graph/degree/id key exceeds 64 bits");
+    Scratch rank_d;
+    TP_CUDA(rank_d.alloc((n + 1) * 4, s));
+    TP_CUDA(dalloc(&g->order, n));
+    TP_CUDA(dalloc(&g->deg, n));
+    if (batched) TP_CUDA(dalloc(&g->graph_of, n));
+    {
+        Scratch a, c, tmp;
+        TP_CUDA(a.alloc(n * 8, s));
+        TP_CUDA(c.alloc(n * 8, s));
+        if (n)
+            vertex_key_kernel<<<grid_for(n), kThreads, 0, s>>>(deg_d.as<uint32_t>(), n, vbase, G, b, bd,
+                                                               a.as<uint64_t>()); ::tp::note_launch();
+        TP_CUDA(cudaGetLastError());
+        cub::DoubleBuffer<uint64_t> kb(a.as<uint64_t>(), c.as<uint64_t>());
+        size_t tb = 0;
+        const int end_bit = gb + bd + b;
+        TP_CUDA(cub::DeviceRadixSort::SortKeys(nullptr, tb, kb, n, 0, end_bit, s));
+        TP_CUDA(tmp.alloc(tb, s));
+        TP_CUDA(cub::DeviceRadixSort::SortKeys(tmp.ptr, tb, kb, n, 0, end_bit, s));
+        if (n)
+            rank_kernel<<<grid_for(n), kThreads, 0, s>>>(kb.Current(), n, b, rank_d.as<uint32_t>(), g->order,
+                                                         deg_d.as<uint32_t>(), g->deg, bd + b, g->graph_of); ::tp::note_launch();
+        TP_CUDA(cudaGetLastError());
+    }
+    deg_d.release();
+
+    // 5. orient + CSR of G+
+    TP_CUDA(dalloc(&g->off, n + 1));
+    TP_CUDA(dalloc(&g->col, m));
+    TP_CUDA(dalloc(&g->ts, m));
+    if (g->has_el) TP_CUDA(dalloc(&g->el, m));
+    TP_CUDA(dalloc(&g->in_off, n + 1));
+    TP_CUDA(dalloc(&g->in_edge, m));
+    {
+        Scratch ok0, ok1, ov1, cnt, tmp;
+        TP_CUDA(ok0.alloc(m * 8, s));
+        TP_CUDA(ok1.alloc(m * 8, s));
+        TP_CUDA(ov1.alloc(m * 8, s));
+        TP_CUDA(cnt.alloc((n + 1) * 4, s));
+        TP_CUDA(cudaMemsetAsync(cnt.ptr, 0, (n + 1) * 4, s));
+        if (m)
+            orient_kernel<<<grid_for(m), kThreads, 0, s>>>(ukey_d.as<uint64_t>(), m, b, rank_d.as<uint32_t>(),
+                                                           ok0.as<uint64_t>(), cnt.as<uint32_t>()); ::tp::note_launch();
+        TP_CUDA(cudaGetLastError());
+        ukey_d.release();
+        rank_d.release();
+        // offsets: exclusive scan of out-degrees (m < 2^32, so 32-bit sums are exact)
+        size_t tb = 0;
+        TP_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tb, cnt.as<uint32_t>(), g->off, n + 1, s));
+        TP_CUDA(tmp.alloc(tb, s));
+        TP_CUDA(cub::DeviceScan::ExclusiveSum(tmp.ptr, tb, cnt.as<uint32_t>(), g->off, n + 1, s));
+        cub::DoubleBuffer<uint64_t> kb(ok0.as<uint64_t>(), ok1.as<uint64_t>());
+        cub::DoubleBuffer<uint64_t> vb(uval_d.as<uint64_t>(), ov1.as<uint64_t>());
+        size_t tb2 = 0;
+        const int end_bit = std::min(64, 2 * b);
+        TP_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tb2, kb, vb, m, 0, end_bit, s));
+        if (tb2 > tb) TP_CUDA(tmp.alloc(tb2, s));
+        TP_CUDA(cub::DeviceRadixSort::SortPairs(tmp.ptr, tb2, kb, vb, m, 0, end_bit, s));
+        // CSR arrays, and keys of the in-edge order
+        Scratch ck0, ck1, cv0, cv1;
+        TP_CUDA(ck0.alloc(m * 8, s));
+        TP_CUDA(ck1.alloc(m * 8, s));
+        TP_CUDA(cv0.alloc(m * 4, s));
+        TP_CUDA(cv1.alloc(m * 4, s));
+        TP_CUDA(cudaMemsetAsync(cnt.ptr, 0, (n + 1) * 4, s));
+        if (m)
+            csr_fill_kernel<<<grid_for(m), kThreads, 0, s>>>(kb.Current(), vb.Current(), m, b, g->col, g->ts, g->el,
+                                                             ck0.as<uint64_t>(), cv0.as<uint32_t>(),
+                                                             cnt.as<uint32_t>()); ::tp::note_launch();
+        TP_CUDA(cudaGetLastError());
+        ok0.release(); ok1.release(); ov1.release(); uval_d.release();
+        TP_CUDA(cub::DeviceScan::ExclusiveSum(tmp.ptr, tb, cnt.as<uint32_t>(), g->in_off, n + 1, s));
+        cub::DoubleBuffer<uint64_t> ckb(ck0.as<uint64_t>(), ck1.as<uint64_t>());
+        cub::DoubleBuffer<uint32_t> cvb(cv0.as<uint32_t>(), cv1.as<uint32_t>());
+        size_t tb3 = 0;
+        TP_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tb3, ckb, cvb, m, 0, end_bit, s));
+        Scratch tmp3;
+        TP_CUDA(tmp3.alloc(tb3, s));
+        TP_CUDA(cub::DeviceRadixSort::SortPairs(tmp3.ptr, tb3, ckb, cvb, m, 0, end_bit, s));
+        if (m)
+            in_edge_fill_kernel<<<grid_for(m), kThreads, 0, s>>>(ckb.Current(), cvb.Current(), m, b, g->off,
+                                                                 g->in_edge); ::tp::note_launch();
+        TP_CUDA(cudaGetLastError());
+    }
+    (void)vmask;
+
+    // 6. vertex labels in position order
+    TP_CUDA(dalloc(&g->vl, n));
+    if (n)
+        vlabel_pos_kernel<<<grid_for(n), kThreads, 0, s>>>((const uint8_t*)vl.dptr, g->order, n, g->vl); ::tp::note_launch();
+    TP_CUDA(cudaGetLastError());
+    if (batched) {
+        TP_CUDA(dalloc(&g->graph_vbase, G + 1));
+        TP_CUDA(cudaMemcpyAsync(g->graph_vbase, vbase_h.data(), (G + 1) * 8ull, cudaMemcpyHostToDevice, s));
+    }
+
+    // 7. statistics
+    {
+        Scratch st;
+        TP_CUDA(st.alloc(32, s));
+        TP_CUDA(cudaMemsetAsync(st.ptr, 0, 32, s));
+        if (n)
+            stats_kernel<<<grid_for(n), kThreads, 0, s>>>(g->off, g->in_off, g->deg, n,
+                                                          st.as<unsigned long long>()); ::tp::note_launch();
+        TP_CUDA(cudaGetLastError());
+        uint64_t h[4];
+        TP_CUDA(cudaMemcpyAsync(h, st.ptr, 32, cudaMemcpyDeviceToHost, s));
+        TP_CUDA(cudaStreamSynchronize(s));
+        tripoll_graph_info& in = g->info;
+        in.num_vertices = n;
+        in.num_input_edges = m_in;
+        in.num_edges = m;
+        in.wedges = h[0];
+        in.q_list_words = h[1];
+        in.dplus_max = h[2];
+        in.degree_max = h[3];
+        in.num_graphs = g->num_graphs;
+        in.num_vlabels = Lv;
+        in.num_elabels = g->has_el ? Le : 0;
+    }
+
+    // 8. the survey plan (work items)
+    if ((rc = build_plan(g, s)) != TRIPOLL_OK) return rc;
+    TP_CUDA(cudaStreamSynchronize(s));
+    g->info.device_bytes = (n + 1) * 8 * 2 + m * (4 + 4 + (g->has_el ? 1 : 0) + sizeof(InEdge)) +
+                           n * (1 + 4 + 4 + (batched ? 4 : 0)) +
+                           (g->n_items_warp + g->n_items_block) * sizeof(WorkItem) + (n + 1) * 8;
+    *out = guard.release();
+    return TRIPOLL_OK;
+}
+
+}  // namespace
+
+void free_graph_arrays(tripoll_graph* g) {
+    cudaFree(g->off); cudaFree(g->col); cudaFree(g->ts); cudaFree(g->el); cudaFree(g->vl);
+    cudaFree(g->deg); cudaFree(g->order); cudaFree(g->graph_of); cudaFree(g->in_off);
+    cudaFree(g->in_edge); cudaFree(g->items_warp); cudaFree(g->items_block); cudaFree(g->pivot_cost);
+    cudaFree(g->graph_vbase);
+    g->off = nullptr; g->col = nullptr; g->ts = nullptr; g->el = nullptr; g->vl = nullptr;
+    g->deg = nullptr; g->order = nullptr; g->graph_of = nullptr; g->in_off = nullptr;
+    g->in_edge = nullptr; g->items_warp = nullptr; g->items_block = nullptr; g->pivot_cost = nullptr;
+    g->graph_vbase = nullptr;
+}
+
+}  // namespace tp
+
+extern "C" int tripoll_graph_create(const uint32_t* src, const uint32_t* dst, const uint32_t* ts,
+                                    const uint8_t* elabel, uint64_t num_edges, const uint8_t* vlabel,
+                                    uint32_t num_vertices, uint32_t num_vlabels, uint32_t num_elabels,
+                                    void* cuda_stream, tripoll_graph_t* out) {
+    return tp::build_impl(src, dst, ts, elabel, num_edges, vlabel, num_vertices, num_vlabels, num_elabels,
+                          nullptr, nullptr, 0, (cudaStream_t)cuda_stream, out);
+}
+
+extern "C" int tripoll_batch_create(const uint32_t* src, const uint32_t* dst, const uint32_t* ts,
+                                    const uint8_t* elabel, const uint64_t* edge_offsets, const uint8_t* vlabel,
+                                    const uint32_t* num_vertices, uint32_t num_graphs, uint32_t num_vlabels,
+                                    uint32_t num_elabels, void* cuda_stream, tripoll_graph_t* out) {
+    if (!edge_offsets || !num_vertices || num_graphs == 0)
+        return tp::fail(TRIPOLL_ERR_INVALID_ARG, "batched build needs edge_offsets, num_vertices, num_graphs > 0");
+    if (edge_offsets[0] != 0) return tp::fail(TRIPOLL_ERR_INVALID_ARG, "edge_offsets[0] must be 0");
+    uint64_t n = 0;
+    for (uint32_t i = 0; i < num_graphs; ++i) {
+        if (edge_offsets[i + 1] < edge_offsets[i])
+            return tp::fail(TRIPOLL_ERR_INVALID_ARG, "edge_offsets must be non-decreasing");
+        n += num_vertices[i];
+    }
+    if (n > 0xFFFFFFFFull) return tp::fail(TRIPOLL_ERR_INVALID_ARG, "too many vertices in the batch");
+    return tp::build_impl(src, dst, ts, elabel, edge_offsets[num_graphs], vlabel, n, num_vlabels, num_elabels,
+                          edge_offsets, num_vertices, num_graphs, (cudaStream_t)cuda_stream, out);
+}

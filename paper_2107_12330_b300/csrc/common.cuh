@@ -1,0 +1,153 @@
+// common.cuh -- shared declarations of the survey library (status handling,
+// the graph object, device helpers).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/tripoll.h"
+
+namespace tp {
+
+// ---- status / error detail -------------------------------------------------------------------
+
+void set_error(const std::string& msg);
+int fail(int status, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define TP_CUDA(call)                                           \
+    do {                                                        \
+        cudaError_t tp_e_ = (call);                             \
+        if (tp_e_ != cudaSuccess) return ::tp::cuda_fail(tp_e_, #call); \
+    } while (0)
+
+// ---- device memory owned by the library --------------------------------------------------------
+
+// Stream-ordered temporary: freed on the stream when it goes out of scope.
+struct Scratch {
+    void* ptr = nullptr;
+    cudaStream_t stream = nullptr;
+    Scratch() = default;
+    Scratch(const Scratch&) = delete;
+    Scratch& operator=(const Scratch&) = delete;
+    ~Scratch() { release(); }
+    cudaError_t alloc(size_t bytes, cudaStream_t s) {
+        release();
+        stream = s;
+        return cudaMallocAsync(&ptr, bytes ? bytes : 16, s);
+    }
+    void release() {
+        if (ptr) cudaFreeAsync(ptr, stream);
+        ptr = nullptr;
+    }
+    template <class T> T* as() const { return static_cast<T*>(ptr); }
+};
+
+// Count of the library's own kernel launches (tripoll_launch_count).
+void note_launch();
+
+// Is p device-accessible memory (device or managed allocation)?
+bool is_device_pointer(const void* p);
+
+// ---- the built graph G+ ------------------------------------------------------------------------
+
+// Edge of the in-edge lists: the directed edge (p,q) at CSR position e, with
+// end = one past the last position of p's out-list.
+struct __align__(16) InEdge {
+    uint32_t e;
+    uint32_t end;
+    uint32_t p;
+    uint32_t pad;
+};
+
+// A unit of survey work: middle vertex q, the part [qlo, qhi) of its out-list
+// staged on chip, and the in-edges [in_lo, in_hi) of q whose pivot suffixes
+// are checked against it.
+struct __align__(16) WorkItem {
+    uint32_t q;
+    uint32_t qlo;     // offset into q's out-list
+    uint32_t qlen;    // staged entries
+    uint32_t in_lo;   // into in_edge[], absolute
+    uint32_t in_hi;
+    uint32_t flags;   // bit 0: chunked (restrict suffix to the staged value range)
+    uint32_t pad0, pad1;
+};
+
+struct GraphDev {
+    uint64_t n = 0, m = 0;
+    const uint64_t* off = nullptr;   // [n+1] out-list offsets, by position in <+
+    const uint32_t* col = nullptr;   // [m] targets (positions), ascending per list
+    const uint32_t* ts = nullptr;    // [m]
+    const uint8_t* el = nullptr;     // [m] or null
+    const uint8_t* vl = nullptr;     // [n] vertex label by position
+    const uint32_t* deg = nullptr;   // [n] degree in the simple graph, by position
+    const uint32_t* order = nullptr; // [n] input vertex id at each position
+    const uint32_t* graph_of = nullptr; // [n] graph index by position (batched) or null
+    const uint64_t* in_off = nullptr;   // [n+1]
+    const InEdge* in_edge = nullptr;    // [m]
+};
+
+}  // namespace tp
+
+struct tripoll_graph {
+    int device = 0;
+    uint64_t n = 0, m = 0, m_in = 0;
+    uint32_t num_graphs = 1;
+    uint32_t Lv = 1, Le = 1;
+    bool has_el = false;
+    // per-graph vertex base in position space is not contiguous; batched builds keep
+    // the input-vertex base of every graph for the local-count output
+    uint64_t* graph_vbase = nullptr;  // device [num_graphs+1] (batched only)
+    // device arrays
+    uint64_t* off = nullptr;
+    uint32_t* col = nullptr;
+    uint32_t* ts = nullptr;
+    uint8_t* el = nullptr;
+    uint8_t* vl = nullptr;
+    uint32_t* deg = nullptr;
+    uint32_t* order = nullptr;
+    uint32_t* graph_of = nullptr;
+    uint64_t* in_off = nullptr;
+    tp::InEdge* in_edge = nullptr;
+    // survey plan
+    tp::WorkItem* items_warp = nullptr;
+    tp::WorkItem* items_block = nullptr;
+    uint64_t n_items_warp = 0, n_items_block = 0;
+    uint64_t* pivot_cost = nullptr;   // [n+1] inclusive prefix of per-pivot cost (for partitioning)
+    // statistics
+    tripoll_graph_info info{};
+
+    tp::GraphDev dev() const {
+        tp::GraphDev g;
+        g.n = n; g.m = m; g.off = off; g.col = col; g.ts = ts; g.el = el; g.vl = vl; g.deg = deg;
+        g.order = order; g.graph_of = graph_of; g.in_off = in_off; g.in_edge = in_edge;
+        return g;
+    }
+};
+
+namespace tp {
+// survey plan limits shared by the builder and the survey kernels
+constexpr uint32_t kWarpMaxQ = 64;      // middle vertices with d+(q) <= this go to the warp kernel
+constexpr uint32_t kBlockChunk = 1024;  // on-chip staged entries of q's out-list per block item
+constexpr uint32_t kWarpInEdges = 32;   // in-edges per warp item
+constexpr uint32_t kBlockInEdges = 256; // in-edges per block item
+
+// layout of one survey result record, in words (absent tables: ~0)
+struct Layout {
+    uint32_t o_count = ~0u, o_hist = ~0u, o_vtri = ~0u, o_etri = ~0u, o_joint = ~0u, o_maxel = ~0u,
+             o_degtri = ~0u;
+    uint64_t o_vlocal = ~0ull;
+    uint64_t words = 0;
+};
+Layout make_layout(uint32_t kinds, uint32_t Lv, uint32_t Le, uint64_t n);
+
+int build_plan(tripoll_graph* g, cudaStream_t s);
+// Launch the survey kernels accumulating into `acc` (zeroed by the caller);
+// counters: device uint32[2] of scratch.
+int launch_survey(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_t t_hi, uint64_t p_lo,
+                  uint64_t p_hi, unsigned long long* acc, uint32_t* counters, cudaStream_t s);
+int check_survey_args(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_t t_hi, const void* result);
+void free_graph_arrays(tripoll_graph* g);
+}  // namespace tp

@@ -1,0 +1,56 @@
+"""The C ABI library loads and exports every entry point include/tripoll.h
+declares; host-only helpers behave as documented (no GPU needed)."""
+import os
+import re
+
+import pytest
+
+import paper_2107_12330_b300 as tp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    with open(os.path.join(ROOT, "include", "tripoll.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(tripoll_[a-z_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = tp.load_library()
+    names = declared_functions()
+    assert len(names) >= 15
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(names) <= set(tp.EXPORTS)
+
+
+def test_result_words_layout():
+    assert tp.tripoll_result_words(tp.TRIPOLL_COUNT, 4, 8) == 1
+    assert tp.tripoll_result_words(tp.TRIPOLL_CLOSURE_HIST, 4, 8) == 33
+    assert tp.tripoll_result_words(1 | 2 | 4, 4, 1) == 1 + 33 + 64
+    assert tp.tripoll_result_words(2 | 8, 16, 8) == 33 + 512
+    assert tp.tripoll_result_words(tp.TRIPOLL_ALL_KINDS, 2, 3, 10) == 1 + 33 + 8 + 27 + 33 * 33 + 3 + 33 ** 3 + 10
+
+
+def test_status_strings():
+    assert tp.tripoll_status_string(0) == "ok"
+    assert "vertex" in tp.tripoll_status_string(tp.TRIPOLL_ERR_VERTEX_RANGE)
+    assert tp.tripoll_status_string(-99) == "unknown status"
+
+
+def test_split_result_views():
+    import numpy as np
+    v = np.arange(1 + 33 + 8, dtype=np.uint64)
+    parts = tp.split_result(v, 1 | 2 | 4, 2, 1)
+    assert parts["count"].tolist() == [0]
+    assert parts["hist"][0] == 1 and len(parts["hist"]) == 33
+    assert len(parts["vtri"]) == 8
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    # no fallback path: without the shared library every call raises
+    monkeypatch.setattr(tp, "_lib", None)
+    with pytest.raises(OSError):
+        tp.load_library(str(tmp_path / "libtripoll.so"))
