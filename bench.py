@@ -98,20 +98,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def algorithmic_bytes(st: dict, triangles_in_window: int) -> int:
-    """Bytes the survey must move per launch (measurement):
-    the compulsory G+ once (offsets 8 B/vertex, label 1 B/vertex, out-list ids,
-    timestamps and edge labels 9 B/edge, in-edge records 16 B/edge), one 4-byte
-    candidate id per wedge check (|W+|), and 5 bytes per triangle for the (p,r)
-    edge's timestamp and label gathered at the hit."""
-    n, m, w = st["num_vertices"], st["num_edges"], st["wedges"]
-    return 9 * n + (9 + 16) * m + 4 * w + 5 * triangles_in_window
+def algorithmic_bytes(st: dict, wedge_checks: int, triangles_in_window: int) -> int:
+    """Bytes one survey launch must move: the compulsory G+ once (offsets and
+    label 9 B per vertex; out-list id, timestamp, edge label and target label
+    10 B and the in-edge record 16 B per edge), one 4-byte candidate id per
+    wedge check of the window, and the (p,r) edge's timestamp and label (5 B)
+    per triangle in the window."""
+    n, m = st["num_vertices"], st["num_edges"]
+    return 9 * n + (10 + 16) * m + 4 * wedge_checks + 5 * triangles_in_window
 
 
 def run_tripoll(args):
     import torch
     import torch.distributed as dist
     import paper_2107_12330_b300 as tp
+    from paper_2107_12330_b300.shard import sharded_survey
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -141,19 +142,21 @@ def run_tripoll(args):
     # shard the pivots across ranks (one graph replica each); one sum at the end
     h0 = build()
     info = tp.tripoll_graph_stats(h0)
+    wedge_checks = tp.tripoll_wedge_checks(h0, t_lo, t_hi, stream=stream)
     bounds = tp.tripoll_partition_pivots(h0, world)
-    p_lo, p_hi = int(bounds[rank]), int(bounds[rank + 1])
     tp.tripoll_destroy(h0)
 
     def step(ev=None):
         h = build()
-        if ev is not None:
-            ev[0].record(stream)
-        tp.tripoll_survey_range(h, kinds, t_lo, t_hi, p_lo, p_hi, result, stream=stream)
-        if ev is not None:
-            ev[1].record(stream)
-        if world > 1:
-            dist.all_reduce(result)
+
+        def survey_range(lo, hi, out):
+            if ev is not None:
+                ev[0].record(stream)
+            tp.tripoll_survey_range(h, kinds, t_lo, t_hi, lo, hi, out, stream=stream)
+            if ev is not None:
+                ev[1].record(stream)
+
+        sharded_survey(survey_range, bounds, rank, result, dist.all_reduce if world > 1 else (lambda x: None))
         tp.tripoll_destroy(h)
 
     for _ in range(args.warmup):
@@ -215,7 +218,7 @@ def run_tripoll(args):
             dist.destroy_process_group()
         return None
     peak, peak_kind = _peaks()
-    alg = algorithmic_bytes(info, triangles)
+    alg = algorithmic_bytes(info, wedge_checks, triangles)
     achieved = alg / (survey_avg * 1e-3) / 1e9
     value = triangles / (ms * 1e-3)
     out = {
@@ -226,12 +229,12 @@ def run_tripoll(args):
                                "ts uniform [0,2^30), vlabel 16, etype Zipf(1.2) over 8; survey = count + "
                                "closure histogram + edge-type triples in window [2^28, 3*2^28-1]",
                    "step": "build G+ from device-resident edge arrays + survey + release",
-                   "input_edges": m_in, "edges": info["num_edges"], "wedges": info["wedges"],
+                   "input_edges": m_in, "edges": info["num_edges"], "wedges": info["wedges"], "wedge_checks_in_window": wedge_checks,
                    "triangles_in_window": triangles, "l2": "inputs larger than L2 (126 MB)",
                    "parallelism": f"pivot shards x{world}"},
         "survey_ms": survey_avg, "build_ms": ms - survey_avg,
         "survey_triangles_per_s": triangles / (survey_avg * 1e-3),
-        "wedge_checks_per_s": info["wedges"] / (survey_avg * 1e-3),
+        "wedge_checks_per_s": wedge_checks / (survey_avg * 1e-3),
         "roofline": {"bound": "hbm", "kernel": "survey (wedge-check + fold kernels, one launch pair)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_source": peak_kind, "algorithmic_bytes": alg, "traffic": None},
@@ -288,18 +291,236 @@ def run_reference(args):
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def batched_inputs(num_graphs):
+    graphs = [synth.batched_graph(i) for i in range(num_graphs)]
+    eoff = np.zeros(num_graphs + 1, np.uint64)
+    eoff[1:] = np.cumsum([g.m_in for g in graphs])
+    nv = np.array([g.n for g in graphs], np.uint32)
+    cat = {k: np.concatenate([getattr(g, k) for g in graphs]) for k in ("src", "dst", "ts", "vlabel")}
+    return graphs, eoff, nv, cat
+
+
+def run_batched(args):
+    """The batched workload: many small graphs built together and surveyed in one
+    launch pair with per-graph records, against one survey launch per graph."""
+    import torch
+    import paper_2107_12330_b300 as tp
+    lib = tp.load_library()
+    dev = torch.device("cuda", 0)
+    kinds = tp.TRIPOLL_COUNT | tp.TRIPOLL_CLOSURE_HIST
+    G = args.graphs
+    graphs, eoff, nv, cat = batched_inputs(G)
+    d = {k: torch.from_numpy(v).to(dev) for k, v in cat.items()}
+    w = tp.tripoll_result_words(kinds, 4, 1, 0)
+    result = torch.zeros(w * G, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def build():
+        return tp.tripoll_batch_create(d["src"], d["dst"], d["ts"], None, eoff, d["vlabel"], nv, 4, 0, stream=stream)
+
+    h0 = build()
+    info = tp.tripoll_graph_stats(h0)
+    wedge_checks = tp.tripoll_wedge_checks(h0, stream=stream)
+    tp.tripoll_destroy(h0)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def step(ev=None):
+        h = build()
+        if ev:
+            ev[0].record(stream)
+        tp.tripoll_survey(h, kinds, 0, 0xFFFFFFFF, result, stream=stream)
+        if ev:
+            ev[1].record(stream)
+        tp.tripoll_destroy(h)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    l0 = lib.tripoll_launch_count()
+    start.record(stream)
+    for k in range(args.steps):
+        step(evs[k])
+    end.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = lib.tripoll_launch_count() - l0
+    ms = start.elapsed_time(end) / args.steps
+    survey_ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    res = result.cpu().numpy().view(np.uint64).reshape(G, w)
+    triangles = int(res[:, 0].sum())
+
+    # one survey launch per graph over the same graphs, each built alone beforehand
+    P = min(G, args.plain_graphs)
+    handles = [tp.tripoll_graph_create(g.src, g.dst, g.ts, None, g.vlabel, g.n, 4, 0) for g in graphs[:P]]
+    outs = torch.zeros(w * P, dtype=torch.int64, device=dev)
+    for i, h in enumerate(handles[:8]):
+        tp.tripoll_survey(h, kinds, 0, 0xFFFFFFFF, outs[i * w:(i + 1) * w], stream=stream)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for i, h in enumerate(handles):
+        tp.tripoll_survey(h, kinds, 0, 0xFFFFFFFF, outs[i * w:(i + 1) * w], stream=stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    plain_survey_ms = a.elapsed_time(b)
+    plain = outs.cpu().numpy().view(np.uint64).reshape(P, w)
+    assert np.array_equal(plain, res[:P]), "batched and per-graph surveys differ"
+    t0 = time.perf_counter()
+    for g in graphs[P:P + args.plain_build_graphs]:
+        h = tp.tripoll_graph_create(g.src, g.dst, g.ts, None, g.vlabel, g.n, 4, 0)
+        tp.tripoll_survey(h, kinds, 0, 0xFFFFFFFF, outs[:w], stream=stream)
+        tp.tripoll_destroy(h)
+    torch.cuda.synchronize()
+    plain_full_s = (time.perf_counter() - t0) / max(1, args.plain_build_graphs)
+    for h in handles:
+        tp.tripoll_destroy(h)
+    batched_graphs_per_s = G / (survey_ms * 1e-3)
+    plain_graphs_per_s = P / (plain_survey_ms * 1e-3)
+    peak, peak_kind = _peaks()
+    alg = algorithmic_bytes(info, wedge_checks, triangles)
+    achieved = alg / (survey_ms * 1e-3) / 1e9
+    return {
+        "metric": "graphs surveyed/s (batched)", "value": G / (ms * 1e-3), "unit": "graphs/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32/u64 integer", "data": "synthetic",
+        "config": {"workload": f"{G} Chung-Lu graphs, exponent 2.5, n log-uniform [32,8192], mean degree "
+                               "uniform [4,64], seeds 0..; ts uniform [0,2^20), vlabel 4; per-graph count + "
+                               "closure histogram", "input_edges": int(eoff[-1]), "edges": info["num_edges"],
+                   "wedges": info["wedges"], "triangles": triangles,
+                   "step": "batched build + one survey launch pair + release"},
+        "triangles_per_s": triangles / (ms * 1e-3), "survey_ms": survey_ms, "build_ms": ms - survey_ms,
+        "survey_graphs_per_s": batched_graphs_per_s,
+        "plain_path": {"graphs": P, "survey_graphs_per_s": plain_graphs_per_s,
+                       "batched_over_plain_survey": batched_graphs_per_s / plain_graphs_per_s,
+                       "build_and_survey_ms_per_graph": plain_full_s * 1e3,
+                       "batched_over_plain_build_and_survey": (G / (ms * 1e-3)) * plain_full_s},
+        "roofline": {"bound": "hbm", "kernel": "survey (one launch pair, all graphs)", "achieved": achieved,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
+                     "algorithmic_bytes": alg, "traffic": None},
+        "clocks": clk, "gpu_launches": int(launches),
+    }
+
+
+def run_serve(args):
+    """The serving workload: resident R-MAT graphs and a Poisson stream of survey
+    requests (4 kinds, random windows), served by the library's continuous-
+    batching server, against one request per launch in arrival order."""
+    import torch
+    import paper_2107_12330_b300 as tp
+    torch.cuda.set_device(0)
+    scales = [int(x) for x in args.serve_scales.split(",")]
+    handles, infos = [], []
+    for i, sc in enumerate(scales):
+        g = synth.rmat_graph(sc, 16, i + 1, ts_bits=24, num_vlabels=16, num_elabels=8)
+        dev = [torch.from_numpy(x).cuda() for x in (g.src, g.dst, g.ts, g.elabel, g.vlabel)]
+        handles.append(tp.tripoll_graph_create(*dev, g.n, 16, 8))
+        infos.append((g.n, sc))
+        del dev
+        torch.cuda.synchronize()
+    kinds_set = [tp.TRIPOLL_COUNT, tp.TRIPOLL_CLOSURE_HIST, tp.TRIPOLL_VLABEL_TRIPLES, tp.TRIPOLL_ELABEL_TRIPLES]
+    R = args.requests
+    draws = [synth.draw(99, 1, i) for i in range(4 * R)]
+    reqs = []
+    for i in range(R):
+        gi = (draws[4 * i] >> 32) * len(scales) >> 32
+        kind = kinds_set[(draws[4 * i + 1] >> 32) * 4 >> 32]
+        lo = (draws[4 * i + 2] >> 40) % (1 << 24 + 1)
+        hi = (draws[4 * i + 3] >> 40) % (1 << 24 + 1)
+        reqs.append((int(gi), kind, int(min(lo, hi)), int(max(lo, hi))))
+    words = [tp.tripoll_result_words(k, 16, 8, infos[gi][0]) for gi, k, _, _ in reqs]
+
+    # one request per launch, in order, each to completion
+    outs_plain = []
+    t0 = time.perf_counter()
+    lat_plain = []
+    for (gi, k, lo, hi), w in zip(reqs, words):
+        o = np.zeros(w, np.uint64)
+        s = time.perf_counter()
+        tp.tripoll_survey(handles[gi], k, lo, hi, o)
+        lat_plain.append(time.perf_counter() - s)
+        outs_plain.append(o)
+    plain_s = time.perf_counter() - t0
+
+    srv = tp.tripoll_server_create(args.scratch_gb << 30, args.max_inflight)
+    slots = [tp.tripoll_server_add_graph(srv, h) for h in handles]
+    # burst: every request queued at once -> throughput
+    t0 = time.perf_counter()
+    ids = [tp.tripoll_server_submit(srv, slots[gi], k, lo, hi) for gi, k, lo, hi in reqs]
+    lat_burst = []
+    for rid, w, want in zip(ids, words, outs_plain):
+        o = np.zeros(w, np.uint64)
+        lat_burst.append(tp.tripoll_server_wait(srv, rid, o, 600000) * 1e-9)
+        assert np.array_equal(o, want), "served result differs from the request alone"
+    served_s = time.perf_counter() - t0
+    # Poisson arrivals at a fraction of the served capacity -> latency under load
+    rate = args.load * R / served_s
+    gaps = [-np.log(1.0 - ((synth.draw(7, 2, i) >> 11) * 2.0 ** -53)) / rate for i in range(R)]
+    ids = []
+    t0 = time.perf_counter()
+    t_next = t0
+    for (gi, k, lo, hi), gap in zip(reqs, gaps):
+        t_next += gap
+        while time.perf_counter() < t_next:
+            pass
+        ids.append(tp.tripoll_server_submit(srv, slots[gi], k, lo, hi))
+    lat_poisson = []
+    for rid, w in zip(ids, words):
+        o = np.zeros(w, np.uint64)
+        lat_poisson.append(tp.tripoll_server_wait(srv, rid, o, 600000) * 1e-9)
+    tp.tripoll_server_destroy(srv)
+    for h in handles:
+        tp.tripoll_destroy(h)
+
+    def pct(x, q):
+        return float(np.percentile(np.array(x) * 1e3, q))
+
+    return {
+        "metric": "survey requests/s (served)", "value": R / served_s, "unit": "requests/s", "n_gpus": 1,
+        "steps": 1, "warmup": 0, "ms_per_step": served_s * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32/u64 integer", "data": "synthetic",
+        "config": {"workload": f"resident R-MAT graphs scales {scales} (edge factor 16, seeds 1..), ts uniform "
+                               "[0,2^24), vlabel 16, etype Zipf(1.2) over 8; requests: kind uniform over count / "
+                               "closure histogram / vertex-label triples / edge-label triples, windows uniform "
+                               "in [0,2^24]", "requests": R, "scratch_cap_gb": args.scratch_gb,
+                   "max_inflight": args.max_inflight},
+        "plain_path": {"requests_per_s": R / plain_s, "p50_ms": pct(lat_plain, 50), "p99_ms": pct(lat_plain, 99)},
+        "served_burst": {"requests_per_s": R / served_s, "p50_ms": pct(lat_burst, 50), "p99_ms": pct(lat_burst, 99)},
+        "served_poisson": {"rate_per_s": rate, "p50_ms": pct(lat_poisson, 50), "p99_ms": pct(lat_poisson, 99)},
+        "served_over_plain": plain_s / served_s,
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="tripoll", choices=["tripoll", "reference"])
+    ap.add_argument("--workload", default="rmat", choices=["rmat", "batched", "serve"])
     ap.add_argument("--scale", type=int, default=24)
     ap.add_argument("--cpu-scale", type=int, default=19)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--graphs", type=int, default=20000)
+    ap.add_argument("--plain-graphs", type=int, default=20000)
+    ap.add_argument("--plain-build-graphs", type=int, default=200)
+    ap.add_argument("--serve-scales", default="16,18,20,22,24,26,16,18")
+    ap.add_argument("--requests", type=int, default=400)
+    ap.add_argument("--scratch-gb", type=int, default=40)
+    ap.add_argument("--max-inflight", type=int, default=32)
+    ap.add_argument("--load", type=float, default=0.7)
     args = ap.parse_args()
-    out = run_reference(args) if args.impl == "reference" else run_tripoll(args)
+    if args.impl == "reference":
+        out = run_reference(args)
+    elif args.workload == "batched":
+        out = run_batched(args)
+    elif args.workload == "serve":
+        out = run_serve(args)
+    else:
+        out = run_tripoll(args)
     if out is not None:
         print(json.dumps(out), flush=True)
 

@@ -170,6 +170,12 @@ int tripoll_partition_pivots(tripoll_graph_t g, uint32_t parts, uint64_t* bounds
 /* Statistics of g.  Host output. */
 int tripoll_graph_stats(tripoll_graph_t g, tripoll_graph_info* info);
 
+/* Number of wedge checks (Sec. 3: a wedge (p,q),(p,r) with q <+ r, checked for
+ * the closing edge (q,r)) that a survey over the window [t_lo, t_hi] performs:
+ * the wedges whose edge (p,q) lies in the window (others cannot close into a
+ * surveyed triangle).  [0, 0xFFFFFFFF] gives |W+|.  *out: host.  Synchronises. */
+int tripoll_wedge_checks(tripoll_graph_t g, uint32_t t_lo, uint32_t t_hi, uint64_t* out, void* cuda_stream);
+
 /* Copy out the built G+ (for checking the builder): any pointer may be NULL.
  *   offsets  uint64[n+1], col uint32[m] (targets as positions in <+), ts
  *   uint32[m], elabel uint8[m], order uint32[n] (input id at each position).

@@ -44,7 +44,7 @@ EXPORTS = (
     "tripoll_survey_range", "tripoll_partition_pivots", "tripoll_graph_stats", "tripoll_graph_export",
     "tripoll_destroy", "tripoll_server_create", "tripoll_server_add_graph", "tripoll_server_submit",
     "tripoll_server_wait", "tripoll_server_destroy", "tripoll_status_string", "tripoll_last_error",
-    "tripoll_launch_count",
+    "tripoll_launch_count", "tripoll_wedge_checks",
 )
 
 
@@ -101,12 +101,13 @@ def load_library(path: str = LIB_PATH):
     lib.tripoll_status_string.restype = ctypes.c_char_p
     lib.tripoll_last_error.argtypes = []
     lib.tripoll_last_error.restype = ctypes.c_char_p
+    lib.tripoll_wedge_checks.argtypes = [vp, u32, u32, ctypes.POINTER(u64), vp]
     lib.tripoll_launch_count.argtypes = []
     lib.tripoll_launch_count.restype = u64
     for name in ("tripoll_graph_create", "tripoll_batch_create", "tripoll_survey", "tripoll_survey_range",
                  "tripoll_partition_pivots", "tripoll_graph_stats", "tripoll_graph_export",
                  "tripoll_server_create", "tripoll_server_add_graph", "tripoll_server_submit",
-                 "tripoll_server_wait"):
+                 "tripoll_server_wait", "tripoll_wedge_checks"):
         getattr(lib, name).restype = i32
     _lib = lib
     return lib
@@ -207,6 +208,14 @@ def tripoll_graph_stats(g):
     info = GraphInfo()
     _check(load_library().tripoll_graph_stats(g, ctypes.byref(info)), "tripoll_graph_stats")
     return info.as_dict()
+
+
+def tripoll_wedge_checks(g, t_lo=0, t_hi=0xFFFFFFFF, stream=None):
+    """Wedge checks a survey over [t_lo, t_hi] performs (|W+| for the full window)."""
+    out = ctypes.c_uint64()
+    _check(load_library().tripoll_wedge_checks(g, t_lo, t_hi, ctypes.byref(out), _stream(stream)),
+           "tripoll_wedge_checks")
+    return out.value
 
 
 def tripoll_graph_export(g, stream=None):

@@ -104,10 +104,38 @@ __global__ void cut_kernel(const uint64_t* __restrict__ prefix, uint64_t n, uint
     bounds[i] = lo;
 }
 
+// wedge checks of a windowed survey: suffix lengths of the in-window in-edges
+__global__ void wedge_checks_kernel(const InEdge* __restrict__ in_edge, uint64_t m, uint32_t t_lo, uint32_t t_hi,
+                                    unsigned long long* out) {
+    unsigned long long w = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
+        const InEdge ie = in_edge[i];
+        if (ie.ts >= t_lo && ie.ts <= t_hi) w += ie.end - ie.e - 1;
+    }
+    for (int o = 16; o; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    if ((threadIdx.x & 31) == 0 && w) atomicAdd(out, w);
+}
+
 }  // namespace
 }  // namespace tp
 
 using namespace tp;
+
+extern "C" int tripoll_wedge_checks(tripoll_graph_t g, uint32_t t_lo, uint32_t t_hi, uint64_t* out, void* cuda_stream) {
+    if (!g || !out || t_lo > t_hi) return fail(TRIPOLL_ERR_INVALID_ARG, "bad wedge_checks arguments");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    Scratch acc;
+    TP_CUDA(acc.alloc(8, s));
+    TP_CUDA(cudaMemsetAsync(acc.ptr, 0, 8, s));
+    if (g->m) {
+        wedge_checks_kernel<<<(unsigned)std::min<uint64_t>((g->m + 255) / 256, 148 * 32), 256, 0, s>>>(
+            g->in_edge, g->m, t_lo, t_hi, acc.as<unsigned long long>()); ::tp::note_launch();
+        TP_CUDA(cudaGetLastError());
+    }
+    TP_CUDA(cudaMemcpyAsync(out, acc.ptr, 8, cudaMemcpyDeviceToHost, s));
+    TP_CUDA(cudaStreamSynchronize(s));
+    return TRIPOLL_OK;
+}
 
 extern "C" const char* tripoll_status_string(int status) {
     switch (status) {

@@ -182,18 +182,24 @@ __global__ void csr_fill_kernel(const uint64_t* __restrict__ okey, const uint64_
     }
 }
 
+// In-edge records of G+ in (target, source) order, carrying the (p,q) edge's
+// metadata and p's label so the survey reads them once per in-edge, coalesced.
 __global__ void in_edge_fill_kernel(const uint64_t* __restrict__ ckey, const uint32_t* __restrict__ cval, uint64_t m,
-                                    int b, const uint64_t* __restrict__ off, InEdge* __restrict__ in_edge) {
+                                    int b, const uint64_t* __restrict__ off, const uint32_t* __restrict__ ts,
+                                    const uint8_t* __restrict__ el, const uint8_t* __restrict__ vl,
+                                    InEdge* __restrict__ in_edge, uint32_t* __restrict__ in_p) {
     const uint64_t mask = (1ull << b) - 1;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m;
          i += (uint64_t)gridDim.x * blockDim.x) {
         uint32_t p = (uint32_t)(ckey[i] & mask);
+        uint32_t e = cval[i];
         InEdge ie;
-        ie.e = cval[i];
+        ie.e = e;
         ie.end = (uint32_t)off[p + 1];
-        ie.p = p;
-        ie.pad = 0;
+        ie.ts = ts[e];
+        ie.meta = (el ? (uint32_t)el[e] : 0u) | ((uint32_t)vl[p] << 8);
         in_edge[i] = ie;
+        in_p[i] = p;
     }
 }
 
@@ -419,13 +425,22 @@ int build_impl(const uint32_t* src_h, const uint32_t* dst_h, const uint32_t* ts_
     }
     deg_d.release();
 
-    // 5. orient + CSR of G+
+    // vertex labels in position order
+    TP_CUDA(dalloc(&g->vl, n));
+    if (n)
+        vlabel_pos_kernel<<<grid_for(n), kThreads, 0, s>>>((const uint8_t*)vl.dptr, g->order, n, g->vl); ::tp::note_launch();
+    TP_CUDA(cudaGetLastError());
+
+    // 5. orient + CSR of G+ (col padded by kColPad entries so 32-byte vector loads
+    //    of the last out-lists stay inside the allocation)
     TP_CUDA(dalloc(&g->off, n + 1));
-    TP_CUDA(dalloc(&g->col, m));
+    TP_CUDA(dalloc(&g->col, m + kColPad));
+    TP_CUDA(cudaMemsetAsync(g->col + m, 0xFF, kColPad * 4, s));
     TP_CUDA(dalloc(&g->ts, m));
     if (g->has_el) TP_CUDA(dalloc(&g->el, m));
     TP_CUDA(dalloc(&g->in_off, n + 1));
     TP_CUDA(dalloc(&g->in_edge, m));
+    TP_CUDA(dalloc(&g->in_p, m));
     {
         Scratch ok0, ok1, ov1, cnt, tmp;
         TP_CUDA(ok0.alloc(m * 8, s));
@@ -474,16 +489,12 @@ int build_impl(const uint32_t* src_h, const uint32_t* dst_h, const uint32_t* ts_
         TP_CUDA(cub::DeviceRadixSort::SortPairs(tmp3.ptr, tb3, ckb, cvb, m, 0, end_bit, s));
         if (m)
             in_edge_fill_kernel<<<grid_for(m), kThreads, 0, s>>>(ckb.Current(), cvb.Current(), m, b, g->off,
-                                                                 g->in_edge); ::tp::note_launch();
+                                                                 g->ts, g->el, g->vl, g->in_edge, g->in_p); ::tp::note_launch();
         TP_CUDA(cudaGetLastError());
     }
     (void)vmask;
 
-    // 6. vertex labels in position order
-    TP_CUDA(dalloc(&g->vl, n));
-    if (n)
-        vlabel_pos_kernel<<<grid_for(n), kThreads, 0, s>>>((const uint8_t*)vl.dptr, g->order, n, g->vl); ::tp::note_launch();
-    TP_CUDA(cudaGetLastError());
+    // 6. batched: vertex base of every graph
     if (batched) {
         TP_CUDA(dalloc(&g->graph_vbase, G + 1));
         TP_CUDA(cudaMemcpyAsync(g->graph_vbase, vbase_h.data(), (G + 1) * 8ull, cudaMemcpyHostToDevice, s));
@@ -517,9 +528,9 @@ int build_impl(const uint32_t* src_h, const uint32_t* dst_h, const uint32_t* ts_
     // 8. the survey plan (work items)
     if ((rc = build_plan(g, s)) != TRIPOLL_OK) return rc;
     TP_CUDA(cudaStreamSynchronize(s));
-    g->info.device_bytes = (n + 1) * 8 * 2 + m * (4 + 4 + (g->has_el ? 1 : 0) + sizeof(InEdge)) +
+    g->info.device_bytes = (n + 1) * 8 * 2 + m * (4 + 4 + (g->has_el ? 1 : 0) + sizeof(InEdge) + 4) +
                            n * (1 + 4 + 4 + (batched ? 4 : 0)) +
-                           (g->n_items_warp + g->n_items_block) * sizeof(WorkItem) + (n + 1) * 8;
+                           (g->n_items_warp + g->n_items_block) * sizeof(WorkItem);
     *out = guard.release();
     return TRIPOLL_OK;
 }
@@ -529,11 +540,11 @@ int build_impl(const uint32_t* src_h, const uint32_t* dst_h, const uint32_t* ts_
 void free_graph_arrays(tripoll_graph* g) {
     cudaFree(g->off); cudaFree(g->col); cudaFree(g->ts); cudaFree(g->el); cudaFree(g->vl);
     cudaFree(g->deg); cudaFree(g->order); cudaFree(g->graph_of); cudaFree(g->in_off);
-    cudaFree(g->in_edge); cudaFree(g->items_warp); cudaFree(g->items_block); cudaFree(g->pivot_cost);
+    cudaFree(g->in_edge); cudaFree(g->in_p); cudaFree(g->items_warp); cudaFree(g->items_block);
     cudaFree(g->graph_vbase);
     g->off = nullptr; g->col = nullptr; g->ts = nullptr; g->el = nullptr; g->vl = nullptr;
     g->deg = nullptr; g->order = nullptr; g->graph_of = nullptr; g->in_off = nullptr;
-    g->in_edge = nullptr; g->items_warp = nullptr; g->items_block = nullptr; g->pivot_cost = nullptr;
+    g->in_edge = nullptr; g->in_p = nullptr; g->items_warp = nullptr; g->items_block = nullptr;
     g->graph_vbase = nullptr;
 }
 

@@ -53,13 +53,14 @@ bool is_device_pointer(const void* p);
 
 // ---- the built graph G+ ------------------------------------------------------------------------
 
-// Edge of the in-edge lists: the directed edge (p,q) at CSR position e, with
-// end = one past the last position of p's out-list.
+// In-edge record: the directed edge (p,q) of G+ at CSR position e, with
+// end = one past the last position of Adj+(p), the edge's timestamp, and
+// meta = edge label | (label of p) << 8.  Sorted by (q, p).
 struct __align__(16) InEdge {
     uint32_t e;
     uint32_t end;
-    uint32_t p;
-    uint32_t pad;
+    uint32_t ts;
+    uint32_t meta;
 };
 
 // A unit of survey work: middle vertex q, the part [qlo, qhi) of its out-list
@@ -87,6 +88,7 @@ struct GraphDev {
     const uint32_t* graph_of = nullptr; // [n] graph index by position (batched) or null
     const uint64_t* in_off = nullptr;   // [n+1]
     const InEdge* in_edge = nullptr;    // [m]
+    const uint32_t* in_p = nullptr;     // [m] pivot p of each in-edge record
 };
 
 }  // namespace tp
@@ -111,18 +113,18 @@ struct tripoll_graph {
     uint32_t* graph_of = nullptr;
     uint64_t* in_off = nullptr;
     tp::InEdge* in_edge = nullptr;
+    uint32_t* in_p = nullptr;
     // survey plan
     tp::WorkItem* items_warp = nullptr;
     tp::WorkItem* items_block = nullptr;
     uint64_t n_items_warp = 0, n_items_block = 0;
-    uint64_t* pivot_cost = nullptr;   // [n+1] inclusive prefix of per-pivot cost (for partitioning)
     // statistics
     tripoll_graph_info info{};
 
     tp::GraphDev dev() const {
         tp::GraphDev g;
         g.n = n; g.m = m; g.off = off; g.col = col; g.ts = ts; g.el = el; g.vl = vl; g.deg = deg;
-        g.order = order; g.graph_of = graph_of; g.in_off = in_off; g.in_edge = in_edge;
+        g.order = order; g.graph_of = graph_of; g.in_off = in_off; g.in_edge = in_edge; g.in_p = in_p;
         return g;
     }
 };
@@ -131,8 +133,9 @@ namespace tp {
 // survey plan limits shared by the builder and the survey kernels
 constexpr uint32_t kWarpMaxQ = 64;      // middle vertices with d+(q) <= this go to the warp kernel
 constexpr uint32_t kBlockChunk = 1024;  // on-chip staged entries of q's out-list per block item
-constexpr uint32_t kWarpInEdges = 32;   // in-edges per warp item
+constexpr uint32_t kWarpInEdges = 64;   // in-edges per warp item
 constexpr uint32_t kBlockInEdges = 256; // in-edges per block item
+constexpr uint32_t kColPad = 8;         // col[] entries past m (0xFFFFFFFF) for 32-byte vector loads
 
 // layout of one survey result record, in words (absent tables: ~0)
 struct Layout {

@@ -15,9 +15,14 @@
 // Two kernels split the middle vertices by |Adj+(q)|: a warp-per-item kernel
 // for short out-lists (each warp its own table) and a block-per-item kernel
 // for long ones (tables of up to kBlockChunk entries; longer out-lists are cut
-// into chunks and each in-edge's suffix is restricted to the chunk's value
-// range).  Items carry at most a fixed number of in-edges so that dynamic
-// scheduling (one atomic per item) keeps all SMs busy to the end.
+// into chunks and each in-edge's segment is restricted to the chunk's value
+// range).  Inside an item the in-edges' segments form one flat index space of
+// wedge checks that warps take in chunks of 32 x kUnroll: consecutive lanes
+// read consecutive suffix entries (coalesced), every lane keeps kUnroll
+// independent loads in flight, and no lane idles however skewed the suffix
+// lengths are.  Triangles outside the time window are pruned
+// before any probe where possible: in-edges (p,q) outside the window get no
+// pieces and entries (q,r) outside it are not inserted.
 //
 // The fold aggregates hits inside a warp with __match_any_sync, then in
 // shared memory, then with 64-bit global atomics once per block -- integer
@@ -67,6 +72,7 @@ struct SurveyArgs {
     uint32_t Lv, Le;
     uint32_t s_words;         // record words mirrored in shared memory (0 for batched graphs)
     uint64_t p_lo, p_hi;      // pivot range
+    bool restricted;          // pivot range is not all of [0, n)
     Layout lay;
     unsigned long long* out;  // accumulator: one record, or num_graphs records (batched)
     uint32_t* counters;       // [2] item counters of the two kernels
@@ -155,73 +161,7 @@ __device__ __forceinline__ void fold_warp(bool keep, const TriMeta& t, const Sur
 
 __device__ __forceinline__ bool in_window(uint32_t t, uint32_t lo, uint32_t hi) { return t >= lo && t <= hi; }
 
-// One warp scans the suffix [j0, end) of Adj+(p) against the staged table of q.
-// Values outside [vlo, vhi] are skipped (chunked tables); the suffix is sorted.
-template <int F>
-__device__ __forceinline__ void scan_suffix(const GraphDev& g, const SurveyArgs& a, uint32_t e_pq, uint32_t j0,
-                                            uint32_t end, uint32_t p, uint32_t q, uint32_t l_q, uint32_t d_q,
-                                            uint32_t vhi, const uint32_t* s_key, const uint16_t* s_pos16,
-                                            const uint8_t* s_pos8, int lg, const uint32_t* s_ts,
-                                            const uint8_t* s_el, const uint8_t* s_vl, const uint32_t* s_deg,
-                                            unsigned long long* s_tab, unsigned long long* grec,
-                                            unsigned long long& cnt) {
-    const int lane = threadIdx.x & 31;
-    const uint32_t tmask = (1u << lg) - 1u;
-    TriMeta t = {};
-    t.t_pq = (F & F_TS) ? __ldg(&g.ts[e_pq]) : 0u;
-    t.e_pq = (F & F_EL) ? __ldg(&g.el[e_pq]) : 0u;
-    t.l_p = (F & F_VL) ? __ldg(&g.vl[p]) : 0u;
-    t.l_q = l_q;
-    t.d_p = (F & F_EXTRA) ? __ldg(&g.deg[p]) : 0u;
-    t.d_q = d_q;
-    t.p = p;
-    t.q = q;
-    if ((F & F_TS) && !in_window(t.t_pq, a.t_lo, a.t_hi)) return;  // no triangle through (p,q) qualifies
-    for (uint32_t base = j0; base < end; base += 128) {
-        uint32_t rr[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            uint32_t j = base + k * 32 + lane;
-            rr[k] = j < end ? __ldg(&g.col[j]) : kEmpty;
-        }
-        bool past = false;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            uint32_t r = rr[k];
-            int pos = -1;
-            if (r != kEmpty && r <= vhi) {
-                uint32_t h = hash_slot(r, lg);
-                while (true) {
-                    uint32_t key = s_key[h];
-                    if (key == r) { pos = s_pos16 ? (int)s_pos16[h] : (int)s_pos8[h]; break; }
-                    if (key == kEmpty) break;
-                    h = (h + 1) & tmask;
-                }
-            }
-            if (r != kEmpty && r > vhi) past = true;
-            bool hit = pos >= 0;
-            if (__any_sync(0xffffffffu, hit)) {
-                bool keep = hit;
-                if (hit) {
-                    uint32_t j = base + k * 32 + lane;
-                    t.r = r;
-                    if (F & F_TS) {
-                        t.t_pr = __ldg(&g.ts[j]);
-                        t.t_qr = s_ts[pos];
-                        keep = in_window(t.t_pr, a.t_lo, a.t_hi) && in_window(t.t_qr, a.t_lo, a.t_hi);
-                    }
-                    if (F & F_EL) { t.e_pr = __ldg(&g.el[j]); t.e_qr = s_el[pos]; }
-                    if (F & F_VL) t.l_r = s_vl[pos];
-                    if (F & F_EXTRA) t.d_r = s_deg[pos];
-                }
-                fold_warp<F>(keep, t, a, s_tab, grec, cnt, g.order);
-            }
-        }
-        if (__any_sync(0xffffffffu, past)) break;
-    }
-}
-
-// Largest-first helper: first index in [lo, hi) with col[idx] >= v.
+// First index in [lo, hi) with col[idx] >= v.
 __device__ __forceinline__ uint32_t lower_bound_col(const uint32_t* __restrict__ col, uint32_t lo, uint32_t hi,
                                                     uint32_t v) {
     while (lo < hi) {
@@ -229,6 +169,193 @@ __device__ __forceinline__ uint32_t lower_bound_col(const uint32_t* __restrict__
         if (__ldg(&col[mid]) < v) lo = mid + 1; else hi = mid;
     }
     return lo;
+}
+
+// ---- on-chip table of Adj+(q) -------------------------------------------------------------
+
+// Open-addressing hash table of the staged part of Adj+(q): key[] holds target
+// positions r (kEmpty = free slot), pos[] the index of r in the staged arrays
+// ts[] (timestamp of (q,r)), el[] (its label), vl[] (label of r), deg[] (d(r)).
+template <class PosT>
+struct QTable {
+    uint32_t* key;
+    PosT* pos;
+    uint32_t* ts;
+    uint32_t* deg;
+    uint8_t* el;
+    uint8_t* vl;
+    int lg;
+};
+
+__device__ __forceinline__ int table_lg(uint32_t len, int lg_min) {
+    int lg = lg_min;
+    while ((1u << lg) < 4u * len) ++lg;  // load factor <= 1/4
+    return lg;
+}
+
+// Insert the entries [i0, len) step `stride` of the staged out-list part at
+// CSR position qbase; entries whose (q,r) timestamp lies outside the window
+// can close no surveyed triangle and are left out.
+template <int F, class PosT>
+__device__ __forceinline__ void table_fill(const GraphDev& g, const SurveyArgs& a, QTable<PosT> T, uint32_t qbase,
+                                           uint32_t len, uint32_t i0, uint32_t stride) {
+    const uint32_t mask = (1u << T.lg) - 1u;
+    for (uint32_t i = i0; i < len; i += stride) {
+        uint32_t t = 0;
+        if (F & F_TS) {
+            t = __ldg(&g.ts[qbase + i]);
+            if (!in_window(t, a.t_lo, a.t_hi)) continue;
+        }
+        const uint32_t r = __ldg(&g.col[qbase + i]);
+        uint32_t h = hash_slot(r, T.lg);
+        while (true) {
+            uint32_t old = atomicCAS(&T.key[h], kEmpty, r);
+            if (old == kEmpty) { T.pos[h] = (PosT)i; break; }
+            h = (h + 1) & mask;
+        }
+        if (F & F_TS) T.ts[i] = t;
+        if (F & F_EL) T.el[i] = __ldg(&g.el[qbase + i]);
+        if (F & F_VL) T.vl[i] = __ldg(&g.vl[r]);
+        if (F & F_EXTRA) T.deg[i] = __ldg(&g.deg[r]);
+    }
+}
+
+// Index of r among the staged entries, or -1.
+template <class PosT>
+__device__ __forceinline__ int table_find(const QTable<PosT>& T, uint32_t r) {
+    const uint32_t mask = (1u << T.lg) - 1u;
+    uint32_t h = hash_slot(r, T.lg);
+    while (true) {
+        const uint32_t key = T.key[h];
+        if (key == r) return (int)T.pos[h];
+        if (key == kEmpty) return -1;
+        h = (h + 1) & mask;
+    }
+}
+
+// ---- in-edges of the item, staged ------------------------------------------------------------
+
+// Per in-edge (p,q) of the item: the segment [j0, jend) of Adj+(p) to check
+// (positions after q, restricted to the staged value range of a chunked
+// item), the (p,q) metadata, and the exclusive prefix pp of the segment
+// lengths: the item's wedge checks form one flat index space [0, pp[n_in]).
+struct InStage {
+    uint32_t* j0;
+    uint32_t* tpq;
+    uint32_t* meta;
+    uint32_t* p;
+    uint32_t* pp;  // [n_in + 1]
+};
+
+__device__ __forceinline__ uint32_t upper_bound_col(const uint32_t* __restrict__ col, uint32_t lo, uint32_t hi,
+                                                    uint32_t v) {
+    while (lo < hi) {
+        uint32_t mid = lo + ((hi - lo) >> 1);
+        if (__ldg(&col[mid]) <= v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Stage in-edge slot k (absolute record kk); returns its segment length.
+template <int F>
+__device__ __forceinline__ uint32_t stage_in_edge(const GraphDev& g, const SurveyArgs& a, InStage S, uint32_t k,
+                                                  uint32_t kk, bool chunked, uint32_t vlo, uint32_t vhi) {
+    const InEdge ie = g.in_edge[kk];
+    bool ok = true;
+    if (F & F_TS) ok = in_window(ie.ts, a.t_lo, a.t_hi);  // (p,q) outside the window: no triangle through it
+    uint32_t p = 0;
+    if (a.restricted || (F & F_EXTRA)) {
+        p = __ldg(&g.in_p[kk]);
+        if (p < a.p_lo || p >= a.p_hi) ok = false;
+    }
+    uint32_t j0 = ie.e + 1, jend = ie.end;
+    if (ok && chunked && j0 < jend) {
+        j0 = lower_bound_col(g.col, j0, jend, vlo);
+        jend = upper_bound_col(g.col, j0, jend, vhi);
+    }
+    S.j0[k] = j0;
+    S.tpq[k] = ie.ts;
+    S.meta[k] = ie.meta;
+    if (F & F_EXTRA) S.p[k] = p;
+    return (ok && j0 < jend) ? jend - j0 : 0u;
+}
+
+// Last slot k in [lo, hi) with pp[k] <= f (pp non-decreasing, pp[lo] <= f).
+__device__ __forceinline__ uint32_t seg_of(const uint32_t* pp, uint32_t lo, uint32_t hi, uint32_t f) {
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (pp[mid] <= f) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+constexpr int kUnroll = 4;  // 32-element groups each lane has in flight
+
+// The calling warp checks the flat wedge indices [f_begin, total) of the item
+// in chunks of 32*kUnroll taken with stride `f_stride`: lane l takes indices
+// f0 + 32u + l, so consecutive lanes read consecutive entries of a pivot
+// suffix (coalesced), and each probes its candidate r in the table of q.
+template <int F, class PosT>
+__device__ __forceinline__ void scan_flat(const GraphDev& g, const SurveyArgs& a, const QTable<PosT>& T,
+                                          const InStage& S, uint32_t n_in, uint32_t total, uint32_t f_begin,
+                                          uint32_t f_stride, uint32_t q, uint32_t l_q, uint32_t d_q,
+                                          unsigned long long* s_tab, unsigned long long* grec,
+                                          unsigned long long& cnt) {
+    const uint32_t lane = threadIdx.x & 31;
+    TriMeta t = {};
+    t.l_q = l_q;
+    t.d_q = d_q;
+    t.q = q;
+    for (uint32_t f0 = f_begin; f0 < total; f0 += f_stride) {
+        // slots of the chunk's first and last index bound every lane's slot
+        uint32_t kb = 0;
+        if (lane == 0) kb = seg_of(S.pp, 0, n_in, f0);
+        if (lane == 31) kb = seg_of(S.pp, 0, n_in, min(f0 + 32 * kUnroll - 1, total - 1));
+        const uint32_t klo = __shfl_sync(0xffffffffu, kb, 0);
+        const uint32_t khi = __shfl_sync(0xffffffffu, kb, 31) + 1;
+        uint32_t r[kUnroll], idx[kUnroll], ks[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const uint32_t f = f0 + 32 * u + lane;
+            ks[u] = kEmpty;
+            r[u] = kEmpty;
+            if (f < total) {
+                const uint32_t k = seg_of(S.pp, klo, khi, f);
+                ks[u] = k;
+                idx[u] = S.j0[k] + (f - S.pp[k]);
+                r[u] = __ldg(&g.col[idx[u]]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int pos = ks[u] != kEmpty ? table_find(T, r[u]) : -1;
+            const bool hit = pos >= 0;
+            if (__any_sync(0xffffffffu, hit)) {
+                bool keep = hit;
+                if (hit) {
+                    const uint32_t k = ks[u];
+                    t.r = r[u];
+                    t.t_pq = S.tpq[k];
+                    const uint32_t meta = S.meta[k];
+                    t.e_pq = meta & 0xffu;
+                    t.l_p = (meta >> 8) & 0xffu;
+                    if (F & F_TS) {
+                        t.t_pr = __ldg(&g.ts[idx[u]]);
+                        t.t_qr = T.ts[pos];
+                        keep = in_window(t.t_pr, a.t_lo, a.t_hi);  // (p,q) and (q,r) were checked at staging
+                    }
+                    if (F & F_EL) { t.e_pr = __ldg(&g.el[idx[u]]); t.e_qr = T.el[pos]; }
+                    if (F & F_VL) t.l_r = T.vl[pos];
+                    if (F & F_EXTRA) {
+                        t.p = S.p[k];
+                        t.d_p = __ldg(&g.deg[t.p]);
+                        t.d_r = T.deg[pos];
+                    }
+                }
+                fold_warp<F>(keep, t, a, s_tab, grec, cnt, g.order);
+            }
+        }
+    }
 }
 
 __device__ __forceinline__ unsigned long long* record_of(const GraphDev& g, const SurveyArgs& a, uint32_t q) {
@@ -248,27 +375,43 @@ __device__ void flush_count(unsigned long long cnt, const SurveyArgs& a, unsigne
 
 // ---- block kernel: one item per block at a time ---------------------------------------------
 
+constexpr uint32_t kBlockTable = 4 * kBlockChunk;
+
+// dynamic shared memory of the block kernel after the record mirror
+constexpr size_t kBlockSmemFixed = kBlockTable * 4 + kBlockChunk * 4 * 2 + kBlockTable * 2 + kBlockChunk * 2 +
+                                   kBlockInEdges * 4 * 4 + (kBlockInEdges + 1) * 4;
+
 template <int F>
 __global__ void __launch_bounds__(kBlockThreads) survey_block_kernel(GraphDev g, const WorkItem* __restrict__ items,
                                                                      uint32_t n_items, SurveyArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
+    using BlockScan = cub::BlockScan<uint32_t, kBlockThreads>;
+    __shared__ typename BlockScan::TempStorage scan_tmp;
+    __shared__ uint32_t s_item, s_total;
+
     unsigned long long* s_tab = reinterpret_cast<unsigned long long*>(smem);
-    uint32_t* s_key = reinterpret_cast<uint32_t*>(smem + a.s_words * 8);
-    uint32_t* s_ts = s_key + 2 * kBlockChunk;
-    uint32_t* s_deg = s_ts + kBlockChunk;
-    uint16_t* s_pos = reinterpret_cast<uint16_t*>(s_deg + kBlockChunk);
-    uint8_t* s_el = reinterpret_cast<uint8_t*>(s_pos + 2 * kBlockChunk);
-    uint8_t* s_vl = s_el + kBlockChunk;
-    __shared__ uint32_t s_item;
+    unsigned char* base = smem + a.s_words * 8;
+    QTable<uint16_t> T;
+    T.key = reinterpret_cast<uint32_t*>(base);
+    T.ts = T.key + kBlockTable;
+    T.deg = T.ts + kBlockChunk;
+    InStage S;
+    S.j0 = T.deg + kBlockChunk;
+    S.tpq = S.j0 + kBlockInEdges;
+    S.meta = S.tpq + kBlockInEdges;
+    S.p = S.meta + kBlockInEdges;
+    S.pp = S.p + kBlockInEdges;
+    T.pos = reinterpret_cast<uint16_t*>(S.pp + kBlockInEdges + 1);
+    T.el = reinterpret_cast<uint8_t*>(T.pos + kBlockTable);
+    T.vl = T.el + kBlockChunk;
 
     for (uint32_t w = threadIdx.x; w < a.s_words; w += blockDim.x) s_tab[w] = 0;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned long long cnt = 0;
     unsigned long long* grec_prev = nullptr;
 
     while (true) {
         if (threadIdx.x == 0) s_item = atomicAdd(&a.counters[1], 1u);
-        __syncthreads();  // also: previous item's table no longer in use
+        __syncthreads();  // also: the previous item's table and stage are no longer read
         const uint32_t it = s_item;
         if (it >= n_items) break;
         const WorkItem item = items[it];
@@ -281,42 +424,27 @@ __global__ void __launch_bounds__(kBlockThreads) survey_block_kernel(GraphDev g,
         grec_prev = grec;
         const uint32_t qbase = (uint32_t)g.off[q] + item.qlo;
         const uint32_t len = item.qlen;
-        int lg = 5;
-        while ((1u << lg) < 2 * len) ++lg;
-        const uint32_t tsize = 1u << lg;
-        for (uint32_t i = threadIdx.x; i < tsize; i += blockDim.x) s_key[i] = kEmpty;
+        T.lg = table_lg(len, 5);
+        const uint32_t tsize = 1u << T.lg;
+        for (uint32_t i = threadIdx.x; i < tsize; i += blockDim.x) T.key[i] = kEmpty;
         __syncthreads();
-        for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) {
-            const uint32_t r = __ldg(&g.col[qbase + i]);
-            uint32_t h = hash_slot(r, lg);
-            while (true) {
-                uint32_t old = atomicCAS(&s_key[h], kEmpty, r);
-                if (old == kEmpty) { s_pos[h] = (uint16_t)i; break; }
-                h = (h + 1) & (tsize - 1);
-            }
-            if (F & F_TS) s_ts[i] = __ldg(&g.ts[qbase + i]);
-            if (F & F_EL) s_el[i] = __ldg(&g.el[qbase + i]);
-            if (F & F_VL) s_vl[i] = __ldg(&g.vl[r]);
-            if (F & F_EXTRA) s_deg[i] = __ldg(&g.deg[r]);
-        }
-        __syncthreads();
+        table_fill<F>(g, a, T, qbase, len, threadIdx.x, blockDim.x);
         const bool chunked = item.flags & 1u;
         const uint32_t vlo = chunked ? __ldg(&g.col[qbase]) : 0u;
-        const uint32_t vhi = chunked ? __ldg(&g.col[qbase + len - 1]) : 0xFFFFFFFEu;
+        const uint32_t vhi = chunked ? __ldg(&g.col[qbase + len - 1]) : 0xFFFFFFFFu;
+        const uint32_t n_in = item.in_hi - item.in_lo;
+        uint32_t np = 0;
+        if (threadIdx.x < n_in) np = stage_in_edge<F>(g, a, S, threadIdx.x, item.in_lo + threadIdx.x, chunked, vlo, vhi);
+        uint32_t pre, total;
+        BlockScan(scan_tmp).ExclusiveSum(np, pre, total);
+        if (threadIdx.x < n_in) S.pp[threadIdx.x] = pre;
+        if (threadIdx.x == 0) { S.pp[n_in] = total; s_total = total; }
+        __syncthreads();
         const uint32_t l_q = (F & F_VL) ? __ldg(&g.vl[q]) : 0u;
         const uint32_t d_q = (F & F_EXTRA) ? __ldg(&g.deg[q]) : 0u;
-        for (uint32_t k = item.in_lo + warp; k < item.in_hi; k += kWarps) {
-            const InEdge ie = g.in_edge[k];
-            if (ie.p < a.p_lo || ie.p >= a.p_hi) continue;
-            uint32_t j0 = ie.e + 1;
-            if (chunked) {
-                uint32_t jj = 0;
-                if (lane == 0) jj = lower_bound_col(g.col, j0, ie.end, vlo);
-                j0 = __shfl_sync(0xffffffffu, jj, 0);
-            }
-            scan_suffix<F>(g, a, ie.e, j0, ie.end, ie.p, q, l_q, d_q, vhi, s_key, s_pos, nullptr, lg, s_ts, s_el,
-                           s_vl, s_deg, s_tab, grec, cnt);
-        }
+        const uint32_t warp = threadIdx.x >> 5;
+        scan_flat<F>(g, a, T, S, n_in, s_total, warp * 32 * kUnroll, kWarps * 32 * kUnroll, q, l_q, d_q, s_tab,
+                     grec, cnt);
     }
     if (grec_prev) flush_count(cnt, a, s_tab, grec_prev);
     __syncthreads();
@@ -325,11 +453,13 @@ __global__ void __launch_bounds__(kBlockThreads) survey_block_kernel(GraphDev g,
 
 // ---- warp kernel: one item per warp at a time ------------------------------------------------
 
-constexpr uint32_t kWTable = 2 * kWarpMaxQ;
+constexpr uint32_t kWTable = 4 * kWarpMaxQ;
 struct WarpSmem {
     uint32_t key[kWTable];
     uint32_t ts[kWarpMaxQ];
     uint32_t deg[kWarpMaxQ];
+    uint32_t j0[kWarpInEdges], tpq[kWarpInEdges], meta[kWarpInEdges], p[kWarpInEdges];
+    uint32_t pp[kWarpInEdges + 1];
     uint8_t pos[kWTable];
     uint8_t el[kWarpMaxQ];
     uint8_t vl[kWarpMaxQ];
@@ -345,6 +475,10 @@ __global__ void __launch_bounds__(kBlockThreads) survey_warp_kernel(GraphDev g, 
     WarpSmem& ws = ws_all[warp];
     for (uint32_t w = threadIdx.x; w < a.s_words; w += blockDim.x) s_tab[w] = 0;
     __syncthreads();
+    QTable<uint8_t> T;
+    T.key = ws.key; T.pos = ws.pos; T.ts = ws.ts; T.deg = ws.deg; T.el = ws.el; T.vl = ws.vl;
+    InStage S;
+    S.j0 = ws.j0; S.tpq = ws.tpq; S.meta = ws.meta; S.p = ws.p; S.pp = ws.pp;
     unsigned long long cnt = 0;
     unsigned long long* grec_prev = nullptr;
 
@@ -363,34 +497,32 @@ __global__ void __launch_bounds__(kBlockThreads) survey_warp_kernel(GraphDev g, 
         grec_prev = grec;
         const uint32_t qbase = (uint32_t)g.off[q];
         const uint32_t len = item.qlen;
-        int lg = 2;
-        while ((1u << lg) < 2 * len) ++lg;
-        const uint32_t tsize = 1u << lg;
+        T.lg = table_lg(len, 2);
+        const uint32_t tsize = 1u << T.lg;
         __syncwarp();
         for (uint32_t i = lane; i < tsize; i += 32) ws.key[i] = kEmpty;
         __syncwarp();
-        for (uint32_t i = lane; i < len; i += 32) {
-            const uint32_t r = __ldg(&g.col[qbase + i]);
-            uint32_t h = hash_slot(r, lg);
-            while (true) {
-                uint32_t old = atomicCAS(&ws.key[h], kEmpty, r);
-                if (old == kEmpty) { ws.pos[h] = (uint8_t)i; break; }
-                h = (h + 1) & (tsize - 1);
-            }
-            if (F & F_TS) ws.ts[i] = __ldg(&g.ts[qbase + i]);
-            if (F & F_EL) ws.el[i] = __ldg(&g.el[qbase + i]);
-            if (F & F_VL) ws.vl[i] = __ldg(&g.vl[r]);
-            if (F & F_EXTRA) ws.deg[i] = __ldg(&g.deg[r]);
+        table_fill<F>(g, a, T, qbase, len, lane, 32);
+        const uint32_t n_in = item.in_hi - item.in_lo;
+        uint32_t np0 = 0, np1 = 0;
+        if ((uint32_t)lane < n_in) np0 = stage_in_edge<F>(g, a, S, lane, item.in_lo + lane, false, 0u, 0u);
+        if ((uint32_t)lane + 32 < n_in)
+            np1 = stage_in_edge<F>(g, a, S, lane + 32, item.in_lo + lane + 32, false, 0u, 0u);
+        // exclusive prefix over slots 0..63 held as (lane, lane + 32)
+        uint32_t x0 = np0, x1 = np1;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y0 = __shfl_up_sync(0xffffffffu, x0, o), y1 = __shfl_up_sync(0xffffffffu, x1, o);
+            if (lane >= o) { x0 += y0; x1 += y1; }
         }
+        const uint32_t half = __shfl_sync(0xffffffffu, x0, 31);
+        const uint32_t total = half + __shfl_sync(0xffffffffu, x1, 31);
+        if ((uint32_t)lane < n_in) ws.pp[lane] = x0 - np0;
+        if ((uint32_t)lane + 32 < n_in) ws.pp[lane + 32] = half + x1 - np1;
+        if (lane == 0) ws.pp[n_in] = total;
         __syncwarp();
         const uint32_t l_q = (F & F_VL) ? __ldg(&g.vl[q]) : 0u;
         const uint32_t d_q = (F & F_EXTRA) ? __ldg(&g.deg[q]) : 0u;
-        for (uint32_t k = item.in_lo; k < item.in_hi; ++k) {
-            const InEdge ie = g.in_edge[k];
-            if (ie.p < a.p_lo || ie.p >= a.p_hi) continue;
-            scan_suffix<F>(g, a, ie.e, ie.e + 1, ie.end, ie.p, q, l_q, d_q, 0xFFFFFFFEu, ws.key, nullptr, ws.pos, lg,
-                           ws.ts, ws.el, ws.vl, ws.deg, s_tab, grec, cnt);
-        }
+        scan_flat<F>(g, a, T, S, n_in, total, 0, 32 * kUnroll, q, l_q, d_q, s_tab, grec, cnt);
     }
     if (grec_prev) flush_count(cnt, a, s_tab, grec_prev);
     __syncthreads();
@@ -474,8 +606,7 @@ void launch_f(const tripoll_graph* g, const SurveyArgs& a, cudaStream_t s, int s
                                                                          (uint32_t)g->n_items_warp, a); ::tp::note_launch();
     }
     if (g->n_items_block) {
-        size_t sm = a.s_words * 8 + (2 * kBlockChunk) * 4 + kBlockChunk * 4 * 2 + (2 * kBlockChunk) * 2 +
-                    kBlockChunk * 2;
+        size_t sm = a.s_words * 8 + kBlockSmemFixed;
         cudaFuncSetAttribute(survey_block_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         int per = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, survey_block_kernel<F>, kBlockThreads, sm);
@@ -537,6 +668,7 @@ int launch_survey(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_
     a.Le = g->Le;
     a.p_lo = p_lo;
     a.p_hi = p_hi;
+    a.restricted = !(p_lo == 0 && p_hi >= g->n);
     a.lay = lay;
     a.out = acc;
     a.counters = counters;

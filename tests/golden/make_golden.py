@@ -29,11 +29,46 @@ RECIPES = {
 }
 
 
+BATCH_KINDS = synth.COUNT | synth.CLOSURE_HIST
+
+
+def _batched_one(i):
+    g = synth.batched_graph(i)
+    r = oracle.survey_graph(g, extras=())
+    return oracle.result_vector(r, BATCH_KINDS, g.num_vlabels, g.num_elabels)
+
+
+def batched(num_graphs, procs):
+    """Per-graph oracle surveys of the batched family, graphs 0..num_graphs-1."""
+    import hashlib
+    import multiprocessing as mp
+    import numpy as np
+    t0 = time.time()
+    with mp.get_context("spawn").Pool(procs) as pool:
+        vecs = pool.map(_batched_one, range(num_graphs), chunksize=64)
+    dt = time.time() - t0
+    allv = np.concatenate(vecs).astype("<u8")
+    out = {"workload": f"batched{num_graphs}", "kinds": BATCH_KINDS, "num_graphs": num_graphs,
+           "words_per_graph": int(vecs[0].shape[0]),
+           "sha256": hashlib.sha256(allv.tobytes()).hexdigest(),
+           "counts": [int(v[0]) for v in vecs],
+           "hist_total": [int(x) for x in allv.reshape(num_graphs, -1)[:, 1:].sum(axis=0)],
+           "oracle_seconds": round(dt, 1), "oracle_procs": procs}
+    path = os.path.join(HERE, f"batched{num_graphs}_survey.json")
+    with open(path, "w") as f:
+        json.dump(out, f)
+    print(path, sum(out["counts"]), f"{dt:.1f}s")
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("name", choices=sorted(RECIPES))
+    ap.add_argument("name", choices=sorted(RECIPES) + ["batched"])
     ap.add_argument("--threads", type=int, default=os.cpu_count())
+    ap.add_argument("--graphs", type=int, default=20000)
     args = ap.parse_args()
+    if args.name == "batched":
+        batched(args.graphs, args.threads)
+        return
     g = RECIPES[args.name]()
     t0 = time.time()
     r = oracle.survey_graph(g, threads=args.threads, extras=())

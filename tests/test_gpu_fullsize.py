@@ -1,0 +1,48 @@
+"""Full-size parity: the benchmark workload (R-MAT scale 24, 268M input edges),
+built and surveyed in the launch configuration bench.py times, against the
+oracle's stored survey (tests/golden/*_survey.json, written by
+tests/golden/make_golden.py from the oracle alone).  Bit-exact."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import synth
+import paper_2107_12330_b300 as tp
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _golden(name):
+    path = os.path.join(HERE, "golden", f"{name}_survey.json")
+    if not os.path.exists(path):
+        pytest.skip(f"no stored survey {path}")
+    with open(path) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("name,make", [("rmat24", synth.rmat24)])
+def test_full_size_survey_matches_stored_oracle(name, make):
+    import torch
+    gold = _golden(name)
+    g = make()
+    assert g.kinds == gold["kinds"] and list(g.window) == gold["window"] and g.m_in == gold["m_in"]
+    dev = [torch.from_numpy(x).cuda() for x in (g.src, g.dst, g.ts, g.elabel, g.vlabel)]
+    h = tp.tripoll_graph_create(*dev, g.n, g.num_vlabels, g.num_elabels)
+    try:
+        st = tp.tripoll_graph_stats(h)
+        w = tp.tripoll_result_words(g.kinds, g.num_vlabels, g.num_elabels, g.n)
+        out = torch.zeros(w, dtype=torch.int64, device="cuda")
+        tp.tripoll_survey(h, g.kinds, g.window[0], g.window[1], out)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().view(np.uint64)
+    finally:
+        tp.tripoll_destroy(h)
+    assert st["num_edges"] == gold["stats"]["m"]
+    assert st["wedges"] == gold["stats"]["wedges"]
+    assert st["dplus_max"] == gold["stats"]["dplus_max"]
+    want = np.array(gold["result"], dtype=np.uint64)
+    bad = np.nonzero(got != want)[0]
+    assert bad.size == 0, f"words {bad[:10].tolist()} differ: gpu {got[bad[:10]].tolist()} oracle {want[bad[:10]].tolist()}"
