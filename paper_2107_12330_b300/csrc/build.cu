@@ -101,13 +101,22 @@ __global__ void unique_count_kernel(const uint64_t* ukey, const uint64_t* runs, 
     *m_out = r;
 }
 
+// Degrees of the simple graph.  Keys are sorted, so the lanes of a warp mostly
+// share the smaller endpoint: those increments are aggregated per warp.
 __global__ void degree_kernel(const uint64_t* __restrict__ ukey, uint64_t m, int b, uint32_t* __restrict__ deg) {
     const uint64_t mask = (1ull << b) - 1;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        uint64_t k = ukey[i];
-        atomicAdd(&deg[k >> b], 1u);
-        atomicAdd(&deg[k & mask], 1u);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t base = blockIdx.x * (uint64_t)blockDim.x; base < m; base += stride) {
+        const uint64_t i = base + threadIdx.x;
+        const bool ok = i < m;
+        const uint64_t k = ok ? ukey[i] : 0;
+        const unsigned act = __ballot_sync(0xffffffffu, ok);
+        if (ok) {
+            const uint32_t u = (uint32_t)(k >> b);
+            const unsigned grp = __match_any_sync(act, u);
+            if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&deg[u], (uint32_t)__popc(grp));
+            atomicAdd(&deg[k & mask], 1u);
+        }
     }
 }
 
@@ -165,41 +174,45 @@ __global__ void orient_kernel(const uint64_t* __restrict__ ukey, uint64_t m, int
     }
 }
 
+// CSR arrays of G+ from the (source, target)-sorted edges, plus, in the same
+// order, the in-edge record of every edge and the key of the in-edge order
+// (the target alone: a stable sort on it keeps sources ascending).
 __global__ void csr_fill_kernel(const uint64_t* __restrict__ okey, const uint64_t* __restrict__ oval, uint64_t m,
-                                int b, uint32_t* __restrict__ col, uint32_t* __restrict__ ts, uint8_t* __restrict__ el,
-                                uint64_t* __restrict__ ckey, uint32_t* __restrict__ cval, uint32_t* __restrict__ din) {
+                                int b, const uint64_t* __restrict__ off, const uint8_t* __restrict__ vl,
+                                uint32_t* __restrict__ col, uint32_t* __restrict__ ts, uint8_t* __restrict__ el,
+                                InEdge* __restrict__ rec, uint32_t* __restrict__ src, uint32_t* __restrict__ ckey,
+                                uint32_t* __restrict__ cval, uint32_t* __restrict__ din) {
     const uint64_t mask = (1ull << b) - 1;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m;
          i += (uint64_t)gridDim.x * blockDim.x) {
-        uint64_t k = okey[i], v = oval[i];
-        uint64_t s = k >> b, d = k & mask;
-        col[i] = (uint32_t)d;
-        ts[i] = (uint32_t)(v >> 8);
-        if (el) el[i] = (uint8_t)(v & 0xffu);
-        ckey[i] = (d << b) | s;
+        const uint64_t k = okey[i], v = oval[i];
+        const uint32_t s = (uint32_t)(k >> b), d = (uint32_t)(k & mask);
+        const uint32_t t = (uint32_t)(v >> 8), l = (uint32_t)(v & 0xffu);
+        col[i] = d;
+        ts[i] = t;
+        if (el) el[i] = (uint8_t)l;
+        InEdge ie;
+        ie.e = (uint32_t)i;
+        ie.end = (uint32_t)off[s + 1];
+        ie.ts = t;
+        ie.meta = l | ((uint32_t)vl[s] << 8);
+        rec[i] = ie;
+        src[i] = s;
+        ckey[i] = d;
         cval[i] = (uint32_t)i;
         atomicAdd(&din[d], 1u);
     }
 }
 
-// In-edge records of G+ in (target, source) order, carrying the (p,q) edge's
-// metadata and p's label so the survey reads them once per in-edge, coalesced.
-__global__ void in_edge_fill_kernel(const uint64_t* __restrict__ ckey, const uint32_t* __restrict__ cval, uint64_t m,
-                                    int b, const uint64_t* __restrict__ off, const uint32_t* __restrict__ ts,
-                                    const uint8_t* __restrict__ el, const uint8_t* __restrict__ vl,
-                                    InEdge* __restrict__ in_edge, uint32_t* __restrict__ in_p) {
-    const uint64_t mask = (1ull << b) - 1;
+// In-edge records in (target, source) order: a gather of the CSR-order records.
+__global__ void in_edge_fill_kernel(const uint32_t* __restrict__ cval, uint64_t m, const InEdge* __restrict__ rec,
+                                    const uint32_t* __restrict__ src, InEdge* __restrict__ in_edge,
+                                    uint32_t* __restrict__ in_p) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m;
          i += (uint64_t)gridDim.x * blockDim.x) {
-        uint32_t p = (uint32_t)(ckey[i] & mask);
-        uint32_t e = cval[i];
-        InEdge ie;
-        ie.e = e;
-        ie.end = (uint32_t)off[p + 1];
-        ie.ts = ts[e];
-        ie.meta = (el ? (uint32_t)el[e] : 0u) | ((uint32_t)vl[p] << 8);
-        in_edge[i] = ie;
-        in_p[i] = p;
+        const uint32_t e = cval[i];
+        in_edge[i] = rec[e];
+        in_p[i] = src[e];
     }
 }
 
@@ -251,15 +264,31 @@ struct Input {
     }
 };
 
-template <class T> cudaError_t dalloc(T** p, uint64_t count) {
-    return cudaMalloc((void**)p, std::max<uint64_t>(count, 1) * sizeof(T));
+// Graph arrays come from the device's stream-ordered pool, which keeps up to a
+// quarter of device memory (at most 64 GiB) cached between builds.
+template <class T> cudaError_t dalloc(T** p, uint64_t count, cudaStream_t s) {
+    return cudaMallocAsync((void**)p, std::max<uint64_t>(count, 1) * sizeof(T), s);
 }
 
-struct GraphGuard {  // frees a half-built graph on any error path
+void retain_pool_memory(int dev) {
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) { cudaGetLastError(); return; }
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { cudaGetLastError(); return; }
+    uint64_t thr = std::min<uint64_t>(total_b / 4, 64ull << 30);
+    if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr) != cudaSuccess) cudaGetLastError();
+}
+
+struct GraphGuard {  // frees a half-built graph on any error path, after the stream's work
     tripoll_graph* g;
-    explicit GraphGuard(tripoll_graph* g_) : g(g_) {}
+    cudaStream_t s;
+    GraphGuard(tripoll_graph* g_, cudaStream_t s_) : g(g_), s(s_) {}
     ~GraphGuard() {
-        if (g) { free_graph_arrays(g); delete g; }
+        if (g) {
+            cudaStreamSynchronize(s);
+            free_graph_arrays(g);
+            delete g;
+        }
     }
     tripoll_graph* release() { tripoll_graph* r = g; g = nullptr; return r; }
 };
@@ -278,6 +307,7 @@ int build_impl(const uint32_t* src_h, const uint32_t* dst_h, const uint32_t* ts_
 
     int dev = 0;
     TP_CUDA(cudaGetDevice(&dev));
+    retain_pool_memory(dev);
     Input src, dst, ts, el, vl;
     int rc;
     if ((rc = src.bind(src_h, m_in * 4, s)) || (rc = dst.bind(dst_h, m_in * 4, s)) ||
@@ -323,7 +353,7 @@ int build_impl(const uint32_t* src_h, const uint32_t* dst_h, const uint32_t* ts_
     const uint64_t sentinel = (2 * b >= 64) ? ~0ull : ((1ull << (2 * b)) - 1);
 
     tripoll_graph* g = new tripoll_graph();
-    GraphGuard guard(g);
+    GraphGuard guard(g, s);
     g->device = dev;
     g->n = n;
     g->m_in = m_in;
@@ -401,9 +431,9 @@ int build_impl(const uint32_t* src_h, const uint32_t* dst_h, const uint32_t* ts_
     if (gb + bd + b > 64) return fail(TRIPOLL_ERR_INVALID_ARG, "graph/degree/id key exceeds 64 bits");
     Scratch rank_d;
     TP_CUDA(rank_d.alloc((n + 1) * 4, s));
-    TP_CUDA(dalloc(&g->order, n));
-    TP_CUDA(dalloc(&g->deg, n));
-    if (batched) TP_CUDA(dalloc(&g->graph_of, n));
+    TP_CUDA(dalloc(&g->order, n, s));
+    TP_CUDA(dalloc(&g->deg, n, s));
+    if (batched) TP_CUDA(dalloc(&g->graph_of, n, s));
     {
         Scratch a, c, tmp;
         TP_CUDA(a.alloc(n * 8, s));
@@ -426,21 +456,21 @@ int build_impl(const uint32_t* src_h, const uint32_t* dst_h, const uint32_t* ts_
     deg_d.release();
 
     // vertex labels in position order
-    TP_CUDA(dalloc(&g->vl, n));
+    TP_CUDA(dalloc(&g->vl, n, s));
     if (n)
         vlabel_pos_kernel<<<grid_for(n), kThreads, 0, s>>>((const uint8_t*)vl.dptr, g->order, n, g->vl); ::tp::note_launch();
     TP_CUDA(cudaGetLastError());
 
     // 5. orient + CSR of G+ (col padded by kColPad entries so 32-byte vector loads
     //    of the last out-lists stay inside the allocation)
-    TP_CUDA(dalloc(&g->off, n + 1));
-    TP_CUDA(dalloc(&g->col, m + kColPad));
+    TP_CUDA(dalloc(&g->off, n + 1, s));
+    TP_CUDA(dalloc(&g->col, m + kColPad, s));
     TP_CUDA(cudaMemsetAsync(g->col + m, 0xFF, kColPad * 4, s));
-    TP_CUDA(dalloc(&g->ts, m));
-    if (g->has_el) TP_CUDA(dalloc(&g->el, m));
-    TP_CUDA(dalloc(&g->in_off, n + 1));
-    TP_CUDA(dalloc(&g->in_edge, m));
-    TP_CUDA(dalloc(&g->in_p, m));
+    TP_CUDA(dalloc(&g->ts, m, s));
+    if (g->has_el) TP_CUDA(dalloc(&g->el, m, s));
+    TP_CUDA(dalloc(&g->in_off, n + 1, s));
+    TP_CUDA(dalloc(&g->in_edge, m, s));
+    TP_CUDA(dalloc(&g->in_p, m, s));
     {
         Scratch ok0, ok1, ov1, cnt, tmp;
         TP_CUDA(ok0.alloc(m * 8, s));
@@ -466,37 +496,41 @@ int build_impl(const uint32_t* src_h, const uint32_t* dst_h, const uint32_t* ts_
         TP_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tb2, kb, vb, m, 0, end_bit, s));
         if (tb2 > tb) TP_CUDA(tmp.alloc(tb2, s));
         TP_CUDA(cub::DeviceRadixSort::SortPairs(tmp.ptr, tb2, kb, vb, m, 0, end_bit, s));
-        // CSR arrays, and keys of the in-edge order
-        Scratch ck0, ck1, cv0, cv1;
-        TP_CUDA(ck0.alloc(m * 8, s));
-        TP_CUDA(ck1.alloc(m * 8, s));
+        // CSR arrays and in-edge records in CSR order; then a stable sort by target
+        Scratch ck0, ck1, cv0, cv1, rec, src;
+        TP_CUDA(ck0.alloc(m * 4, s));
+        TP_CUDA(ck1.alloc(m * 4, s));
         TP_CUDA(cv0.alloc(m * 4, s));
         TP_CUDA(cv1.alloc(m * 4, s));
+        TP_CUDA(rec.alloc(m * sizeof(InEdge), s));
+        TP_CUDA(src.alloc(m * 4, s));
         TP_CUDA(cudaMemsetAsync(cnt.ptr, 0, (n + 1) * 4, s));
         if (m)
-            csr_fill_kernel<<<grid_for(m), kThreads, 0, s>>>(kb.Current(), vb.Current(), m, b, g->col, g->ts, g->el,
-                                                             ck0.as<uint64_t>(), cv0.as<uint32_t>(),
+            csr_fill_kernel<<<grid_for(m), kThreads, 0, s>>>(kb.Current(), vb.Current(), m, b, g->off, g->vl, g->col,
+                                                             g->ts, g->el, rec.as<InEdge>(), src.as<uint32_t>(),
+                                                             ck0.as<uint32_t>(), cv0.as<uint32_t>(),
                                                              cnt.as<uint32_t>()); ::tp::note_launch();
         TP_CUDA(cudaGetLastError());
         ok0.release(); ok1.release(); ov1.release(); uval_d.release();
         TP_CUDA(cub::DeviceScan::ExclusiveSum(tmp.ptr, tb, cnt.as<uint32_t>(), g->in_off, n + 1, s));
-        cub::DoubleBuffer<uint64_t> ckb(ck0.as<uint64_t>(), ck1.as<uint64_t>());
+        cub::DoubleBuffer<uint32_t> ckb(ck0.as<uint32_t>(), ck1.as<uint32_t>());
         cub::DoubleBuffer<uint32_t> cvb(cv0.as<uint32_t>(), cv1.as<uint32_t>());
         size_t tb3 = 0;
-        TP_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tb3, ckb, cvb, m, 0, end_bit, s));
+        const int tbits = std::min(32, b);
+        TP_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tb3, ckb, cvb, m, 0, tbits, s));
         Scratch tmp3;
         TP_CUDA(tmp3.alloc(tb3, s));
-        TP_CUDA(cub::DeviceRadixSort::SortPairs(tmp3.ptr, tb3, ckb, cvb, m, 0, end_bit, s));
+        TP_CUDA(cub::DeviceRadixSort::SortPairs(tmp3.ptr, tb3, ckb, cvb, m, 0, tbits, s));
         if (m)
-            in_edge_fill_kernel<<<grid_for(m), kThreads, 0, s>>>(ckb.Current(), cvb.Current(), m, b, g->off,
-                                                                 g->ts, g->el, g->vl, g->in_edge, g->in_p); ::tp::note_launch();
+            in_edge_fill_kernel<<<grid_for(m), kThreads, 0, s>>>(cvb.Current(), m, rec.as<InEdge>(),
+                                                                 src.as<uint32_t>(), g->in_edge, g->in_p); ::tp::note_launch();
         TP_CUDA(cudaGetLastError());
     }
     (void)vmask;
 
     // 6. batched: vertex base of every graph
     if (batched) {
-        TP_CUDA(dalloc(&g->graph_vbase, G + 1));
+        TP_CUDA(dalloc(&g->graph_vbase, G + 1, s));
         TP_CUDA(cudaMemcpyAsync(g->graph_vbase, vbase_h.data(), (G + 1) * 8ull, cudaMemcpyHostToDevice, s));
     }
 
@@ -537,11 +571,12 @@ int build_impl(const uint32_t* src_h, const uint32_t* dst_h, const uint32_t* ts_
 
 }  // namespace
 
+// Arrays return to the pool in the order of the legacy default stream.
 void free_graph_arrays(tripoll_graph* g) {
-    cudaFree(g->off); cudaFree(g->col); cudaFree(g->ts); cudaFree(g->el); cudaFree(g->vl);
-    cudaFree(g->deg); cudaFree(g->order); cudaFree(g->graph_of); cudaFree(g->in_off);
-    cudaFree(g->in_edge); cudaFree(g->in_p); cudaFree(g->items_warp); cudaFree(g->items_block);
-    cudaFree(g->graph_vbase);
+    void* arrays[] = {g->off, g->col, g->ts, g->el, g->vl, g->deg, g->order, g->graph_of, g->in_off,
+                      g->in_edge, g->in_p, g->items_warp, g->items_block, g->graph_vbase};
+    for (void* a : arrays)
+        if (a) cudaFreeAsync(a, 0);
     g->off = nullptr; g->col = nullptr; g->ts = nullptr; g->el = nullptr; g->vl = nullptr;
     g->deg = nullptr; g->order = nullptr; g->graph_of = nullptr; g->in_off = nullptr;
     g->in_edge = nullptr; g->in_p = nullptr; g->items_warp = nullptr; g->items_block = nullptr;

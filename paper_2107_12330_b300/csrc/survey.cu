@@ -17,19 +17,23 @@
 // for long ones (tables of up to kBlockChunk entries; longer out-lists are cut
 // into chunks and each in-edge's segment is restricted to the chunk's value
 // range).  Inside an item the in-edges' segments form one flat index space of
-// wedge checks that warps take in chunks of 32 x kUnroll: consecutive lanes
+// wedge checks that warps split evenly and walk in chunks of 32 x kUnroll: consecutive lanes
 // read consecutive suffix entries (coalesced), every lane keeps kUnroll
 // independent loads in flight, and no lane idles however skewed the suffix
-// lengths are.  Triangles outside the time window are pruned
-// before any probe where possible: in-edges (p,q) outside the window get no
-// pieces and entries (q,r) outside it are not inserted.
+// lengths are.  Triangles outside the time window are pruned before any
+// probe where possible: in-edges (p,q) outside the window get empty segments
+// and entries (q,r) outside it are not inserted.
 //
-// The fold aggregates hits inside a warp with __match_any_sync, then in
-// shared memory, then with 64-bit global atomics once per block -- integer
-// adds commute, so the result is exact and schedule-independent.
+// Hits are queued per warp and folded 32 at a time, one per lane; the fold
+// aggregates inside the warp with __match_any_sync, then in shared memory,
+// then with 64-bit global atomics once per block -- integer adds commute, so
+// the result is exact and schedule-independent.
 #include <cub/cub.cuh>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "common.cuh"
 
@@ -290,36 +294,92 @@ __device__ __forceinline__ uint32_t seg_of(const uint32_t* pp, uint32_t lo, uint
 }
 
 constexpr int kUnroll = 4;  // 32-element groups each lane has in flight
+constexpr int kHitQ = 64;   // per-warp queue of hits awaiting the fold
 
-// The calling warp checks the flat wedge indices [f_begin, total) of the item
-// in chunks of 32*kUnroll taken with stride `f_stride`: lane l takes indices
-// f0 + 32u + l, so consecutive lanes read consecutive entries of a pivot
-// suffix (coalesced), and each probes its candidate r in the table of q.
+// Per-warp queue of wedge checks that hit: CSR position of (p,r), and
+// (staged index of r) | (in-edge slot) << 16.
+struct HitQueue {
+    uint32_t* idx;
+    uint32_t* pk;
+};
+
+// Fold the first `nq` queued hits, one per lane (nq <= 32).
+template <int F, class PosT>
+__device__ __forceinline__ void fold_queue(const GraphDev& g, const SurveyArgs& a, const QTable<PosT>& T,
+                                           const InStage& S, const HitQueue& H, uint32_t nq, TriMeta t,
+                                           unsigned long long* s_tab, unsigned long long* grec,
+                                           unsigned long long& cnt) {
+    const uint32_t lane = threadIdx.x & 31;
+    bool keep = lane < nq;
+    if (keep) {
+        const uint32_t idx = H.idx[lane], pk = H.pk[lane];
+        const uint32_t pos = pk & 0xffffu, k = pk >> 16;
+        t.t_pq = S.tpq[k];
+        const uint32_t meta = S.meta[k];
+        t.e_pq = meta & 0xffu;
+        t.l_p = (meta >> 8) & 0xffu;
+        if (F & F_TS) {
+            t.t_pr = __ldg(&g.ts[idx]);
+            t.t_qr = T.ts[pos];
+            keep = in_window(t.t_pr, a.t_lo, a.t_hi);  // (p,q) and (q,r) were checked at staging
+        }
+        if (F & F_EL) { t.e_pr = __ldg(&g.el[idx]); t.e_qr = T.el[pos]; }
+        if (F & F_VL) t.l_r = T.vl[pos];
+        if (F & F_EXTRA) {
+            t.r = __ldg(&g.col[idx]);
+            t.p = S.p[k];
+            t.d_p = __ldg(&g.deg[t.p]);
+            t.d_r = T.deg[pos];
+        }
+    }
+    fold_warp<F>(keep, t, a, s_tab, grec, cnt, g.order);
+}
+
+// The calling warp checks the flat wedge indices [f_begin, f_end) of the
+// item in consecutive chunks of 32*kUnroll: lane l takes indices f0 + 32u + l,
+// so consecutive lanes read consecutive entries of a pivot suffix (coalesced),
+// and each probes its candidate r in the table of q.  The in-edge slots a
+// chunk spans are found from the previous chunk's with one ballot.  Hits are
+// queued and folded 32 at a time, one per lane.
 template <int F, class PosT>
 __device__ __forceinline__ void scan_flat(const GraphDev& g, const SurveyArgs& a, const QTable<PosT>& T,
-                                          const InStage& S, uint32_t n_in, uint32_t total, uint32_t f_begin,
-                                          uint32_t f_stride, uint32_t q, uint32_t l_q, uint32_t d_q,
+                                          const InStage& S, const HitQueue& H, uint32_t n_in, uint32_t f_begin,
+                                          uint32_t f_end, uint32_t q, uint32_t l_q, uint32_t d_q,
                                           unsigned long long* s_tab, unsigned long long* grec,
                                           unsigned long long& cnt) {
     const uint32_t lane = threadIdx.x & 31;
+    const uint32_t lt_mask = (1u << lane) - 1u;
     TriMeta t = {};
     t.l_q = l_q;
     t.d_q = d_q;
     t.q = q;
-    for (uint32_t f0 = f_begin; f0 < total; f0 += f_stride) {
-        // slots of the chunk's first and last index bound every lane's slot
+    uint32_t nq = 0;  // queued hits (warp-uniform)
+    uint32_t klo = 0;  // slot holding the chunk's first index
+    {
         uint32_t kb = 0;
-        if (lane == 0) kb = seg_of(S.pp, 0, n_in, f0);
-        if (lane == 31) kb = seg_of(S.pp, 0, n_in, min(f0 + 32 * kUnroll - 1, total - 1));
-        const uint32_t klo = __shfl_sync(0xffffffffu, kb, 0);
-        const uint32_t khi = __shfl_sync(0xffffffffu, kb, 31) + 1;
+        if (lane == 0 && f_begin < f_end) kb = seg_of(S.pp, 0, n_in, f_begin);
+        klo = __shfl_sync(0xffffffffu, kb, 0);
+    }
+    for (uint32_t f0 = f_begin; f0 < f_end; f0 += 32 * kUnroll) {
+        // khi: first slot after klo whose prefix passes the chunk's last index (pp[n_in] = total)
+        const uint32_t fl = min(f0 + 32 * kUnroll - 1, f_end - 1);
+        uint32_t khi = 0;
+        for (uint32_t base = klo + 1;; base += 32) {
+            const uint32_t sl = base + lane;
+            const unsigned bm = __ballot_sync(0xffffffffu, sl > n_in || S.pp[sl] > fl);
+            if (bm) {
+                khi = base + __ffs(bm) - 1;
+                break;
+            }
+        }
         uint32_t r[kUnroll], idx[kUnroll], ks[kUnroll];
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
             const uint32_t f = f0 + 32 * u + lane;
             ks[u] = kEmpty;
             r[u] = kEmpty;
-            if (f < total) {
+            idx[u] = 0;
+            if (f < f_end) {
                 const uint32_t k = seg_of(S.pp, klo, khi, f);
                 ks[u] = k;
                 idx[u] = S.j0[k] + (f - S.pp[k]);
@@ -329,33 +389,34 @@ __device__ __forceinline__ void scan_flat(const GraphDev& g, const SurveyArgs& a
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
             const int pos = ks[u] != kEmpty ? table_find(T, r[u]) : -1;
-            const bool hit = pos >= 0;
-            if (__any_sync(0xffffffffu, hit)) {
-                bool keep = hit;
-                if (hit) {
-                    const uint32_t k = ks[u];
-                    t.r = r[u];
-                    t.t_pq = S.tpq[k];
-                    const uint32_t meta = S.meta[k];
-                    t.e_pq = meta & 0xffu;
-                    t.l_p = (meta >> 8) & 0xffu;
-                    if (F & F_TS) {
-                        t.t_pr = __ldg(&g.ts[idx[u]]);
-                        t.t_qr = T.ts[pos];
-                        keep = in_window(t.t_pr, a.t_lo, a.t_hi);  // (p,q) and (q,r) were checked at staging
-                    }
-                    if (F & F_EL) { t.e_pr = __ldg(&g.el[idx[u]]); t.e_qr = T.el[pos]; }
-                    if (F & F_VL) t.l_r = T.vl[pos];
-                    if (F & F_EXTRA) {
-                        t.p = S.p[k];
-                        t.d_p = __ldg(&g.deg[t.p]);
-                        t.d_r = T.deg[pos];
-                    }
+            const unsigned hm = __ballot_sync(0xffffffffu, pos >= 0);
+            if (hm) {
+                if (pos >= 0) {
+                    const uint32_t slot = nq + __popc(hm & lt_mask);
+                    H.idx[slot] = idx[u];
+                    H.pk[slot] = (uint32_t)pos | (ks[u] << 16);
                 }
-                fold_warp<F>(keep, t, a, s_tab, grec, cnt, g.order);
+                nq += __popc(hm);
+                if (nq >= 32) {
+                    __syncwarp();
+                    fold_queue<F>(g, a, T, S, H, 32, t, s_tab, grec, cnt);
+                    __syncwarp();
+                    nq -= 32;
+                    if (lane < nq) {
+                        H.idx[lane] = H.idx[32 + lane];
+                        H.pk[lane] = H.pk[32 + lane];
+                    }
+                    __syncwarp();
+                }
             }
         }
+        klo = khi - 1;
     }
+    if (nq) {
+        __syncwarp();
+        fold_queue<F>(g, a, T, S, H, nq, t, s_tab, grec, cnt);
+    }
+    __syncwarp();
 }
 
 __device__ __forceinline__ unsigned long long* record_of(const GraphDev& g, const SurveyArgs& a, uint32_t q) {
@@ -378,7 +439,8 @@ __device__ void flush_count(unsigned long long cnt, const SurveyArgs& a, unsigne
 constexpr uint32_t kBlockTable = 4 * kBlockChunk;
 
 // dynamic shared memory of the block kernel after the record mirror
-constexpr size_t kBlockSmemFixed = kBlockTable * 4 + kBlockChunk * 4 * 2 + kBlockTable * 2 + kBlockChunk * 2 +
+constexpr size_t kBlockSmemFixed = kWarps * kHitQ * 8 + kBlockTable * 4 + kBlockChunk * 4 * 2 + kBlockTable * 2 +
+                                   kBlockChunk * 2 +
                                    kBlockInEdges * 4 * 4 + (kBlockInEdges + 1) * 4;
 
 template <int F>
@@ -401,7 +463,11 @@ __global__ void __launch_bounds__(kBlockThreads) survey_block_kernel(GraphDev g,
     S.meta = S.tpq + kBlockInEdges;
     S.p = S.meta + kBlockInEdges;
     S.pp = S.p + kBlockInEdges;
-    T.pos = reinterpret_cast<uint16_t*>(S.pp + kBlockInEdges + 1);
+    uint32_t* hq = S.pp + kBlockInEdges + 1;
+    HitQueue H;
+    H.idx = hq + (threadIdx.x >> 5) * 2 * kHitQ;
+    H.pk = H.idx + kHitQ;
+    T.pos = reinterpret_cast<uint16_t*>(hq + kWarps * 2 * kHitQ);
     T.el = reinterpret_cast<uint8_t*>(T.pos + kBlockTable);
     T.vl = T.el + kBlockChunk;
 
@@ -443,7 +509,9 @@ __global__ void __launch_bounds__(kBlockThreads) survey_block_kernel(GraphDev g,
         const uint32_t l_q = (F & F_VL) ? __ldg(&g.vl[q]) : 0u;
         const uint32_t d_q = (F & F_EXTRA) ? __ldg(&g.deg[q]) : 0u;
         const uint32_t warp = threadIdx.x >> 5;
-        scan_flat<F>(g, a, T, S, n_in, s_total, warp * 32 * kUnroll, kWarps * 32 * kUnroll, q, l_q, d_q, s_tab,
+        const uint32_t f_begin = (uint32_t)(((uint64_t)s_total * warp) / kWarps);
+        const uint32_t f_end = (uint32_t)(((uint64_t)s_total * (warp + 1)) / kWarps);
+        scan_flat<F>(g, a, T, S, H, n_in, f_begin, f_end, q, l_q, d_q, s_tab,
                      grec, cnt);
     }
     if (grec_prev) flush_count(cnt, a, s_tab, grec_prev);
@@ -460,6 +528,7 @@ struct WarpSmem {
     uint32_t deg[kWarpMaxQ];
     uint32_t j0[kWarpInEdges], tpq[kWarpInEdges], meta[kWarpInEdges], p[kWarpInEdges];
     uint32_t pp[kWarpInEdges + 1];
+    uint32_t qidx[kHitQ], qpk[kHitQ];
     uint8_t pos[kWTable];
     uint8_t el[kWarpMaxQ];
     uint8_t vl[kWarpMaxQ];
@@ -522,7 +591,10 @@ __global__ void __launch_bounds__(kBlockThreads) survey_warp_kernel(GraphDev g, 
         __syncwarp();
         const uint32_t l_q = (F & F_VL) ? __ldg(&g.vl[q]) : 0u;
         const uint32_t d_q = (F & F_EXTRA) ? __ldg(&g.deg[q]) : 0u;
-        scan_flat<F>(g, a, T, S, n_in, total, 0, 32 * kUnroll, q, l_q, d_q, s_tab, grec, cnt);
+        HitQueue H;
+        H.idx = ws.qidx;
+        H.pk = ws.qpk;
+        scan_flat<F>(g, a, T, S, H, n_in, 0, total, q, l_q, d_q, s_tab, grec, cnt);
     }
     if (grec_prev) flush_count(cnt, a, s_tab, grec_prev);
     __syncthreads();
@@ -592,25 +664,40 @@ unsigned grid_n(uint64_t items) {
     return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(b, 148u * 64u));
 }
 
+// Resident blocks per SM of a kernel at a dynamic shared-memory size, with the
+// kernel's shared-memory limit raised once; cached per (kernel, size, device).
+int blocks_per_sm(const void* kernel, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::tuple<const void*, size_t, int>, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    auto key = std::make_tuple(kernel, smem, dev);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kBlockThreads, smem);
+    per = std::max(per, 1);
+    cache[key] = per;
+    return per;
+}
+
 template <int F>
 void launch_f(const tripoll_graph* g, const SurveyArgs& a, cudaStream_t s, int sms) {
     GraphDev gd = g->dev();
     if (g->n_items_warp) {
         size_t sm = ((a.s_words * 8 + 15) & ~15u) + kWarps * sizeof(WarpSmem);
-        cudaFuncSetAttribute(survey_warp_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        int per = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, survey_warp_kernel<F>, kBlockThreads, sm);
-        uint64_t blocks = (uint64_t)std::max(per, 1) * sms;
+        const int per = blocks_per_sm((const void*)survey_warp_kernel<F>, sm);
+        uint64_t blocks = (uint64_t)per * sms;
         blocks = std::min<uint64_t>(blocks, (g->n_items_warp + kWarps - 1) / kWarps);
         survey_warp_kernel<F><<<(unsigned)blocks, kBlockThreads, sm, s>>>(gd, g->items_warp,
                                                                          (uint32_t)g->n_items_warp, a); ::tp::note_launch();
     }
     if (g->n_items_block) {
         size_t sm = a.s_words * 8 + kBlockSmemFixed;
-        cudaFuncSetAttribute(survey_block_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        int per = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, survey_block_kernel<F>, kBlockThreads, sm);
-        uint64_t blocks = (uint64_t)std::max(per, 1) * sms;
+        const int per = blocks_per_sm((const void*)survey_block_kernel<F>, sm);
+        uint64_t blocks = (uint64_t)per * sms;
         blocks = std::min<uint64_t>(blocks, g->n_items_block);
         survey_block_kernel<F><<<(unsigned)blocks, kBlockThreads, sm, s>>>(gd, g->items_block,
                                                                           (uint32_t)g->n_items_block, a); ::tp::note_launch();
@@ -647,8 +734,8 @@ int build_plan(tripoll_graph* g, cudaStream_t s) {
     TP_CUDA(cudaStreamSynchronize(s));
     g->n_items_warp = tot[0];
     g->n_items_block = tot[1];
-    TP_CUDA(cudaMalloc((void**)&g->items_warp, std::max<uint64_t>(1, tot[0]) * sizeof(WorkItem)));
-    TP_CUDA(cudaMalloc((void**)&g->items_block, std::max<uint64_t>(1, tot[1]) * sizeof(WorkItem)));
+    TP_CUDA(cudaMallocAsync((void**)&g->items_warp, std::max<uint64_t>(1, tot[0]) * sizeof(WorkItem), s));
+    TP_CUDA(cudaMallocAsync((void**)&g->items_block, std::max<uint64_t>(1, tot[1]) * sizeof(WorkItem), s));
     if (n)
         plan_fill_kernel<<<grid_n(n), 256, 0, s>>>(g->off, g->in_off, n, ow.as<uint32_t>(), ob.as<uint32_t>(),
                                                    g->items_warp, g->items_block); ::tp::note_launch();
