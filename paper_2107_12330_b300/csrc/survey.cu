@@ -82,8 +82,9 @@ struct SurveyArgs {
     uint32_t* counters;       // [2] item counters of the two kernels
 };
 
-__device__ __forceinline__ uint32_t hash_slot(uint32_t r, int lg) {
-    return (r * 2654435761u) >> (32 - lg);
+// Home slot of r in a table of `size` slots: a multiplicative hash scaled to size.
+__device__ __forceinline__ uint32_t hash_slot(uint32_t r, uint32_t size) {
+    return __umulhi(r * 2654435761u, size);
 }
 
 // ceil(log2(d)) for d >= 2, and 0 for d in {0, 1}: the closing/opening-time bin (Alg. 4)
@@ -188,14 +189,10 @@ struct QTable {
     uint32_t* deg;
     uint8_t* el;
     uint8_t* vl;
-    int lg;
+    uint32_t size;  // slots: 3 per staged entry (load factor <= 1/3)
 };
 
-__device__ __forceinline__ int table_lg(uint32_t len, int lg_min) {
-    int lg = lg_min;
-    while ((1u << lg) < 4u * len) ++lg;  // load factor <= 1/4
-    return lg;
-}
+__device__ __forceinline__ uint32_t table_size(uint32_t len) { return max(3u * len, 4u); }
 
 // Insert the entries [i0, len) step `stride` of the staged out-list part at
 // CSR position qbase; entries whose (q,r) timestamp lies outside the window
@@ -203,7 +200,6 @@ __device__ __forceinline__ int table_lg(uint32_t len, int lg_min) {
 template <int F, class PosT>
 __device__ __forceinline__ void table_fill(const GraphDev& g, const SurveyArgs& a, QTable<PosT> T, uint32_t qbase,
                                            uint32_t len, uint32_t i0, uint32_t stride) {
-    const uint32_t mask = (1u << T.lg) - 1u;
     for (uint32_t i = i0; i < len; i += stride) {
         uint32_t t = 0;
         if (F & F_TS) {
@@ -211,11 +207,11 @@ __device__ __forceinline__ void table_fill(const GraphDev& g, const SurveyArgs& 
             if (!in_window(t, a.t_lo, a.t_hi)) continue;
         }
         const uint32_t r = __ldg(&g.col[qbase + i]);
-        uint32_t h = hash_slot(r, T.lg);
+        uint32_t h = hash_slot(r, T.size);
         while (true) {
             uint32_t old = atomicCAS(&T.key[h], kEmpty, r);
             if (old == kEmpty) { T.pos[h] = (PosT)i; break; }
-            h = (h + 1) & mask;
+            if (++h == T.size) h = 0;
         }
         if (F & F_TS) T.ts[i] = t;
         if (F & F_EL) T.el[i] = __ldg(&g.el[qbase + i]);
@@ -227,13 +223,12 @@ __device__ __forceinline__ void table_fill(const GraphDev& g, const SurveyArgs& 
 // Index of r among the staged entries, or -1.
 template <class PosT>
 __device__ __forceinline__ int table_find(const QTable<PosT>& T, uint32_t r) {
-    const uint32_t mask = (1u << T.lg) - 1u;
-    uint32_t h = hash_slot(r, T.lg);
+    uint32_t h = hash_slot(r, T.size);
     while (true) {
         const uint32_t key = T.key[h];
         if (key == r) return (int)T.pos[h];
         if (key == kEmpty) return -1;
-        h = (h + 1) & mask;
+        if (++h == T.size) h = 0;
     }
 }
 
@@ -241,10 +236,13 @@ __device__ __forceinline__ int table_find(const QTable<PosT>& T, uint32_t r) {
 
 // Per in-edge (p,q) of the item: the segment [j0, jend) of Adj+(p) to check
 // (positions after q, restricted to the staged value range of a chunked
-// item), the (p,q) metadata, and the exclusive prefix pp of the segment
-// lengths: the item's wedge checks form one flat index space [0, pp[n_in]).
+// item), the (p,q) metadata, and the exclusive prefix pp of the segments'
+// quad counts, a quad being 4 consecutive positions starting at a multiple of
+// 4: the item's wedge checks form one flat index space of quads
+// [0, pp[n_in]), each quad read with one 16-byte load.
 struct InStage {
     uint32_t* j0;
+    uint32_t* jend;
     uint32_t* tpq;
     uint32_t* meta;
     uint32_t* p;
@@ -260,7 +258,7 @@ __device__ __forceinline__ uint32_t upper_bound_col(const uint32_t* __restrict__
     return lo;
 }
 
-// Stage in-edge slot k (absolute record kk); returns its segment length.
+// Stage in-edge slot k (absolute record kk); returns its segment's quad count.
 template <int F>
 __device__ __forceinline__ uint32_t stage_in_edge(const GraphDev& g, const SurveyArgs& a, InStage S, uint32_t k,
                                                   uint32_t kk, bool chunked, uint32_t vlo, uint32_t vhi) {
@@ -278,10 +276,11 @@ __device__ __forceinline__ uint32_t stage_in_edge(const GraphDev& g, const Surve
         jend = upper_bound_col(g.col, j0, jend, vhi);
     }
     S.j0[k] = j0;
+    S.jend[k] = jend;
     S.tpq[k] = ie.ts;
     S.meta[k] = ie.meta;
     if (F & F_EXTRA) S.p[k] = p;
-    return (ok && j0 < jend) ? jend - j0 : 0u;
+    return (ok && j0 < jend) ? ((jend + 3) >> 2) - (j0 >> 2) : 0u;
 }
 
 // Last slot k in [lo, hi) with pp[k] <= f (pp non-decreasing, pp[lo] <= f).
@@ -293,7 +292,7 @@ __device__ __forceinline__ uint32_t seg_of(const uint32_t* pp, uint32_t lo, uint
     return lo;
 }
 
-constexpr int kUnroll = 4;  // 32-element groups each lane has in flight
+constexpr int kUnroll = 2;  // quads each lane has in flight per chunk (8 positions)
 constexpr int kHitQ = 64;   // per-warp queue of hits awaiting the fold
 
 // Per-warp queue of wedge checks that hit: CSR position of (p,r), and
@@ -335,12 +334,41 @@ __device__ __forceinline__ void fold_queue(const GraphDev& g, const SurveyArgs& 
     fold_warp<F>(keep, t, a, s_tab, grec, cnt, g.order);
 }
 
-// The calling warp checks the flat wedge indices [f_begin, f_end) of the
-// item in consecutive chunks of 32*kUnroll: lane l takes indices f0 + 32u + l,
-// so consecutive lanes read consecutive entries of a pivot suffix (coalesced),
-// and each probes its candidate r in the table of q.  The in-edge slots a
-// chunk spans are found from the previous chunk's with one ballot.  Hits are
-// queued and folded 32 at a time, one per lane.
+// Queue this lane's hit (pos >= 0) at CSR position idx of slot k; fold the
+// queue when 32 hits are waiting.  Called by the whole warp.
+template <int F, class PosT>
+__device__ __forceinline__ void push_hit(int pos, uint32_t idx, uint32_t k, uint32_t& nq, const GraphDev& g,
+                                         const SurveyArgs& a, const QTable<PosT>& T, const InStage& S,
+                                         const HitQueue& H, const TriMeta& t, unsigned long long* s_tab,
+                                         unsigned long long* grec, unsigned long long& cnt) {
+    const uint32_t lane = threadIdx.x & 31;
+    const unsigned hm = __ballot_sync(0xffffffffu, pos >= 0);
+    if (!hm) return;
+    if (pos >= 0) {
+        const uint32_t slot = nq + __popc(hm & ((1u << lane) - 1u));
+        H.idx[slot] = idx;
+        H.pk[slot] = (uint32_t)pos | (k << 16);
+    }
+    nq += __popc(hm);
+    if (nq >= 32) {
+        __syncwarp();
+        fold_queue<F>(g, a, T, S, H, 32, t, s_tab, grec, cnt);
+        __syncwarp();
+        nq -= 32;
+        if (lane < nq) {
+            H.idx[lane] = H.idx[32 + lane];
+            H.pk[lane] = H.pk[32 + lane];
+        }
+        __syncwarp();
+    }
+}
+
+// The calling warp checks the flat quad indices [f_begin, f_end) of the item
+// in consecutive chunks of 32*kUnroll quads: lane l takes quads f0 + 32u + l,
+// so consecutive lanes read consecutive 16-byte quads of a pivot suffix
+// (coalesced), and each probes the quad's candidates r in the table of q.
+// The in-edge slots a chunk spans are found from the previous chunk's with
+// one ballot.  Hits are queued and folded 32 at a time, one per lane.
 template <int F, class PosT>
 __device__ __forceinline__ void scan_flat(const GraphDev& g, const SurveyArgs& a, const QTable<PosT>& T,
                                           const InStage& S, const HitQueue& H, uint32_t n_in, uint32_t f_begin,
@@ -348,20 +376,19 @@ __device__ __forceinline__ void scan_flat(const GraphDev& g, const SurveyArgs& a
                                           unsigned long long* s_tab, unsigned long long* grec,
                                           unsigned long long& cnt) {
     const uint32_t lane = threadIdx.x & 31;
-    const uint32_t lt_mask = (1u << lane) - 1u;
     TriMeta t = {};
     t.l_q = l_q;
     t.d_q = d_q;
     t.q = q;
-    uint32_t nq = 0;  // queued hits (warp-uniform)
-    uint32_t klo = 0;  // slot holding the chunk's first index
+    uint32_t nq = 0;   // queued hits (warp-uniform)
+    uint32_t klo = 0;  // slot holding the chunk's first quad
     {
         uint32_t kb = 0;
         if (lane == 0 && f_begin < f_end) kb = seg_of(S.pp, 0, n_in, f_begin);
         klo = __shfl_sync(0xffffffffu, kb, 0);
     }
     for (uint32_t f0 = f_begin; f0 < f_end; f0 += 32 * kUnroll) {
-        // khi: first slot after klo whose prefix passes the chunk's last index (pp[n_in] = total)
+        // khi: first slot after klo whose prefix passes the chunk's last quad (pp[n_in] = total)
         const uint32_t fl = min(f0 + 32 * kUnroll - 1, f_end - 1);
         uint32_t khi = 0;
         for (uint32_t base = klo + 1;; base += 32) {
@@ -372,42 +399,33 @@ __device__ __forceinline__ void scan_flat(const GraphDev& g, const SurveyArgs& a
                 break;
             }
         }
-        uint32_t r[kUnroll], idx[kUnroll], ks[kUnroll];
+        uint4 v[kUnroll];
+        uint32_t e0[kUnroll], lo[kUnroll], hi[kUnroll], ks[kUnroll];
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
             const uint32_t f = f0 + 32 * u + lane;
-            ks[u] = kEmpty;
-            r[u] = kEmpty;
-            idx[u] = 0;
+            ks[u] = 0;
+            lo[u] = 1;
+            hi[u] = 0;  // empty unless f is in range
+            e0[u] = 0;
             if (f < f_end) {
                 const uint32_t k = seg_of(S.pp, klo, khi, f);
+                const uint32_t j0 = S.j0[k];
                 ks[u] = k;
-                idx[u] = S.j0[k] + (f - S.pp[k]);
-                r[u] = __ldg(&g.col[idx[u]]);
+                e0[u] = ((j0 >> 2) + (f - S.pp[k])) << 2;
+                lo[u] = j0;
+                hi[u] = S.jend[k];
+                v[u] = __ldg(reinterpret_cast<const uint4*>(g.col + e0[u]));
             }
         }
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
-            const int pos = ks[u] != kEmpty ? table_find(T, r[u]) : -1;
-            const unsigned hm = __ballot_sync(0xffffffffu, pos >= 0);
-            if (hm) {
-                if (pos >= 0) {
-                    const uint32_t slot = nq + __popc(hm & lt_mask);
-                    H.idx[slot] = idx[u];
-                    H.pk[slot] = (uint32_t)pos | (ks[u] << 16);
-                }
-                nq += __popc(hm);
-                if (nq >= 32) {
-                    __syncwarp();
-                    fold_queue<F>(g, a, T, S, H, 32, t, s_tab, grec, cnt);
-                    __syncwarp();
-                    nq -= 32;
-                    if (lane < nq) {
-                        H.idx[lane] = H.idx[32 + lane];
-                        H.pk[lane] = H.pk[32 + lane];
-                    }
-                    __syncwarp();
-                }
+            const uint32_t rr[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const uint32_t e = e0[u] + i;
+                const int pos = (e >= lo[u] && e < hi[u]) ? table_find(T, rr[i]) : -1;
+                push_hit<F>(pos, e, ks[u], nq, g, a, T, S, H, t, s_tab, grec, cnt);
             }
         }
         klo = khi - 1;
@@ -436,12 +454,16 @@ __device__ void flush_count(unsigned long long cnt, const SurveyArgs& a, unsigne
 
 // ---- block kernel: one item per block at a time ---------------------------------------------
 
-constexpr uint32_t kBlockTable = 4 * kBlockChunk;
+constexpr uint32_t kBlockTable = 3 * kBlockChunk;
 
 // dynamic shared memory of the block kernel after the record mirror
-constexpr size_t kBlockSmemFixed = kWarps * kHitQ * 8 + kBlockTable * 4 + kBlockChunk * 4 * 2 + kBlockTable * 2 +
-                                   kBlockChunk * 2 +
-                                   kBlockInEdges * 4 * 4 + (kBlockInEdges + 1) * 4;
+// dynamic shared memory of the block kernel after the record mirror (the
+// degree array of staged entries only for kinds that use degrees)
+template <int F>
+constexpr size_t block_smem_fixed() {
+    return kWarps * kHitQ * 8 + kBlockTable * 4 + kBlockChunk * 4 * ((F & F_EXTRA) ? 2 : 1) + kBlockTable * 2 +
+           kBlockChunk * 2 + kBlockInEdges * 4 * 5 + (kBlockInEdges + 1) * 4;
+}
 
 template <int F>
 __global__ void __launch_bounds__(kBlockThreads) survey_block_kernel(GraphDev g, const WorkItem* __restrict__ items,
@@ -456,10 +478,11 @@ __global__ void __launch_bounds__(kBlockThreads) survey_block_kernel(GraphDev g,
     QTable<uint16_t> T;
     T.key = reinterpret_cast<uint32_t*>(base);
     T.ts = T.key + kBlockTable;
-    T.deg = T.ts + kBlockChunk;
+    T.deg = T.ts + kBlockChunk;  // present only with F_EXTRA
     InStage S;
-    S.j0 = T.deg + kBlockChunk;
-    S.tpq = S.j0 + kBlockInEdges;
+    S.j0 = T.deg + ((F & F_EXTRA) ? kBlockChunk : 0);
+    S.jend = S.j0 + kBlockInEdges;
+    S.tpq = S.jend + kBlockInEdges;
     S.meta = S.tpq + kBlockInEdges;
     S.p = S.meta + kBlockInEdges;
     S.pp = S.p + kBlockInEdges;
@@ -490,8 +513,8 @@ __global__ void __launch_bounds__(kBlockThreads) survey_block_kernel(GraphDev g,
         grec_prev = grec;
         const uint32_t qbase = (uint32_t)g.off[q] + item.qlo;
         const uint32_t len = item.qlen;
-        T.lg = table_lg(len, 5);
-        const uint32_t tsize = 1u << T.lg;
+        T.size = table_size(len);
+        const uint32_t tsize = T.size;
         for (uint32_t i = threadIdx.x; i < tsize; i += blockDim.x) T.key[i] = kEmpty;
         __syncthreads();
         table_fill<F>(g, a, T, qbase, len, threadIdx.x, blockDim.x);
@@ -521,12 +544,12 @@ __global__ void __launch_bounds__(kBlockThreads) survey_block_kernel(GraphDev g,
 
 // ---- warp kernel: one item per warp at a time ------------------------------------------------
 
-constexpr uint32_t kWTable = 4 * kWarpMaxQ;
+constexpr uint32_t kWTable = 3 * kWarpMaxQ;
 struct WarpSmem {
     uint32_t key[kWTable];
     uint32_t ts[kWarpMaxQ];
     uint32_t deg[kWarpMaxQ];
-    uint32_t j0[kWarpInEdges], tpq[kWarpInEdges], meta[kWarpInEdges], p[kWarpInEdges];
+    uint32_t j0[kWarpInEdges], jend[kWarpInEdges], tpq[kWarpInEdges], meta[kWarpInEdges], p[kWarpInEdges];
     uint32_t pp[kWarpInEdges + 1];
     uint32_t qidx[kHitQ], qpk[kHitQ];
     uint8_t pos[kWTable];
@@ -547,7 +570,7 @@ __global__ void __launch_bounds__(kBlockThreads) survey_warp_kernel(GraphDev g, 
     QTable<uint8_t> T;
     T.key = ws.key; T.pos = ws.pos; T.ts = ws.ts; T.deg = ws.deg; T.el = ws.el; T.vl = ws.vl;
     InStage S;
-    S.j0 = ws.j0; S.tpq = ws.tpq; S.meta = ws.meta; S.p = ws.p; S.pp = ws.pp;
+    S.j0 = ws.j0; S.jend = ws.jend; S.tpq = ws.tpq; S.meta = ws.meta; S.p = ws.p; S.pp = ws.pp;
     unsigned long long cnt = 0;
     unsigned long long* grec_prev = nullptr;
 
@@ -566,8 +589,8 @@ __global__ void __launch_bounds__(kBlockThreads) survey_warp_kernel(GraphDev g, 
         grec_prev = grec;
         const uint32_t qbase = (uint32_t)g.off[q];
         const uint32_t len = item.qlen;
-        T.lg = table_lg(len, 2);
-        const uint32_t tsize = 1u << T.lg;
+        T.size = table_size(len);
+        const uint32_t tsize = T.size;
         __syncwarp();
         for (uint32_t i = lane; i < tsize; i += 32) ws.key[i] = kEmpty;
         __syncwarp();
@@ -695,7 +718,7 @@ void launch_f(const tripoll_graph* g, const SurveyArgs& a, cudaStream_t s, int s
                                                                          (uint32_t)g->n_items_warp, a); ::tp::note_launch();
     }
     if (g->n_items_block) {
-        size_t sm = a.s_words * 8 + kBlockSmemFixed;
+        size_t sm = a.s_words * 8 + block_smem_fixed<F>();
         const int per = blocks_per_sm((const void*)survey_block_kernel<F>, sm);
         uint64_t blocks = (uint64_t)per * sms;
         blocks = std::min<uint64_t>(blocks, g->n_items_block);
