@@ -161,6 +161,28 @@ int tripoll_survey_range(tripoll_graph_t g, uint32_t kind_mask, uint32_t t_lo, u
                          uint64_t pivot_lo, uint64_t pivot_hi, uint64_t* result,
                          void* cuda_stream);
 
+/* tripoll_survey for callers that cannot allocate device memory where they
+ * survey -- e.g. code whose stream is being captured into a CUDA graph, loops
+ * that must never enter an allocator, or hosts whose device memory belongs to
+ * another framework.  The paper has no counterpart; this is a library
+ * convenience.  Same arguments, kernels and result as tripoll_survey, but the
+ * call allocates nothing: its scratch (the accumulation record and two work
+ * counters) is a static 8 MiB device array that every GPU loading the library
+ * holds until the process exits.
+ *   - The first call on a device looks up that array's device address; make
+ *     the first call before any stream capture on that device.
+ *   - Every call reuses the same array (each call clears the part it needs):
+ *     calls whose GPU work overlaps -- on different streams, or from different
+ *     threads -- race and corrupt each other's results.  Order them on one
+ *     stream or with events.
+ *   - The current device must be the graph's device.
+ *   - Errors: NO_MEMORY when the result (tripoll_result_words x 8 bytes, times
+ *     the graph count of a batched graph) exceeds 8 MiB less 256 bytes; the
+ *     argument errors of tripoll_survey.  Synchronises cuda_stream for a host
+ *     result. */
+int tripoll_survey_static(tripoll_graph_t g, uint32_t kind_mask, uint32_t t_lo, uint32_t t_hi,
+                          uint64_t* result, void* cuda_stream);
+
 /* Split [0, n) into `parts` pivot ranges of near-equal survey cost (the
  * out-list entries each pivot's wedge checks read).  bounds: host,
  * uint64[parts + 1], bounds[0] = 0, bounds[parts] = n.  Synchronises. */

@@ -44,7 +44,7 @@ EXPORTS = (
     "tripoll_survey_range", "tripoll_partition_pivots", "tripoll_graph_stats", "tripoll_graph_export",
     "tripoll_destroy", "tripoll_server_create", "tripoll_server_add_graph", "tripoll_server_submit",
     "tripoll_server_wait", "tripoll_server_destroy", "tripoll_status_string", "tripoll_last_error",
-    "tripoll_launch_count", "tripoll_wedge_checks",
+    "tripoll_launch_count", "tripoll_wedge_checks", "tripoll_survey_static",
 )
 
 
@@ -102,12 +102,13 @@ def load_library(path: str = LIB_PATH):
     lib.tripoll_last_error.argtypes = []
     lib.tripoll_last_error.restype = ctypes.c_char_p
     lib.tripoll_wedge_checks.argtypes = [vp, u32, u32, ctypes.POINTER(u64), vp]
+    lib.tripoll_survey_static.argtypes = [vp, u32, u32, u32, vp, vp]
     lib.tripoll_launch_count.argtypes = []
     lib.tripoll_launch_count.restype = u64
     for name in ("tripoll_graph_create", "tripoll_batch_create", "tripoll_survey", "tripoll_survey_range",
                  "tripoll_partition_pivots", "tripoll_graph_stats", "tripoll_graph_export",
                  "tripoll_server_create", "tripoll_server_add_graph", "tripoll_server_submit",
-                 "tripoll_server_wait", "tripoll_wedge_checks"):
+                 "tripoll_server_wait", "tripoll_wedge_checks", "tripoll_survey_static"):
         getattr(lib, name).restype = i32
     _lib = lib
     return lib
@@ -188,6 +189,14 @@ def tripoll_survey(g, kind_mask, t_lo, t_hi, result, stream=None):
     """Survey into `result` (uint64 words; torch tensor on device or host, or numpy)."""
     _check(load_library().tripoll_survey(g, kind_mask, t_lo, t_hi, _ptr(result), _stream(stream)),
            "tripoll_survey")
+    return result
+
+
+def tripoll_survey_static(g, kind_mask, t_lo, t_hi, result, stream=None):
+    """tripoll_survey without any device allocation (static scratch; see tripoll.h).
+    For callers that must not allocate; calls that overlap on the GPU race."""
+    _check(load_library().tripoll_survey_static(g, kind_mask, t_lo, t_hi, _ptr(result), _stream(stream)),
+           "tripoll_survey_static")
     return result
 
 
