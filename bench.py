@@ -98,6 +98,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# DRAM traffic of the survey per algorithmic byte, from the last ncu capture of
+# survey_block_kernel (profiles/survey_block_kernel_rmat22_ncu.md: 16.93 GB read
+# for 17.18 GB algorithmic at scale 22), valid only for the survey source it was
+# taken on (first 16 hex digits of its SHA-256); any other source reports null.
+PROFILED_SURVEY = {"sha256_16": "5d16502c80e898e4", "dram_per_alg_byte": 16.937e9 / 17.184e9,
+                   "capture": "ncu, survey_block_kernel, R-MAT scale 22, scaled by algorithmic bytes"}
+
+
+def survey_traffic(alg_bytes: int):
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2107_12330_b300", "csrc", "survey.cu"), "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    if sha != PROFILED_SURVEY["sha256_16"]:
+        return None, "survey source changed since the last ncu capture"
+    return alg_bytes * PROFILED_SURVEY["dram_per_alg_byte"], PROFILED_SURVEY["capture"]
+
+
 def algorithmic_bytes(st: dict, wedge_checks: int, triangles_in_window: int) -> int:
     """Bytes one survey launch must move: the compulsory G+ once (offsets and
     label 9 B per vertex; out-list id, timestamp, edge label and target label
@@ -220,6 +237,7 @@ def run_tripoll(args):
     peak, peak_kind = _peaks()
     alg = algorithmic_bytes(info, wedge_checks, triangles)
     achieved = alg / (survey_avg * 1e-3) / 1e9
+    traffic, traffic_src = survey_traffic(alg)
     value = triangles / (ms * 1e-3)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -237,7 +255,8 @@ def run_tripoll(args):
         "wedge_checks_per_s": wedge_checks / (survey_avg * 1e-3),
         "roofline": {"bound": "hbm", "kernel": "survey (wedge-check + fold kernels, one launch pair)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "peak_source": peak_kind, "algorithmic_bytes": alg, "traffic": None},
+                     "peak_source": peak_kind, "algorithmic_bytes": alg, "traffic": traffic,
+                     "traffic_source": traffic_src},
         "clocks": clk, "gpu_launches": int(launches), "e2e": e2e,
     }
     if world == 1 and not args.no_cpu_baseline:
