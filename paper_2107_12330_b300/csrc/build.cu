@@ -13,8 +13,8 @@
 //   orient     every edge directed from the <+ -smaller end; sorted by
 //              (source position, target position): the out-lists Adj+ (CSR)
 //              with timestamps and edge labels aligned to them (Adj+^m)
-//   in-edges   the same edges sorted by (target, source): for every middle
-//              vertex q the directed edges (p,q) that end at it
+//   in-edges   16-byte records of the same edges, stably sorted by target: for
+//              every middle vertex q the directed edges (p,q) that end at it
 //   stats      |E+|, |W+| = sum C(d+,2), d+ max, ...
 #include <cub/cub.cuh>
 
@@ -180,8 +180,7 @@ __global__ void orient_kernel(const uint64_t* __restrict__ ukey, uint64_t m, int
 __global__ void csr_fill_kernel(const uint64_t* __restrict__ okey, const uint64_t* __restrict__ oval, uint64_t m,
                                 int b, const uint64_t* __restrict__ off, const uint8_t* __restrict__ vl,
                                 uint32_t* __restrict__ col, uint32_t* __restrict__ ts, uint8_t* __restrict__ el,
-                                InEdge* __restrict__ rec, uint32_t* __restrict__ src, uint32_t* __restrict__ ckey,
-                                uint32_t* __restrict__ cval, uint32_t* __restrict__ din) {
+                                InEdge* __restrict__ rec, uint32_t* __restrict__ ckey, uint32_t* __restrict__ din) {
     const uint64_t mask = (1ull << b) - 1;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m;
          i += (uint64_t)gridDim.x * blockDim.x) {
@@ -197,22 +196,8 @@ __global__ void csr_fill_kernel(const uint64_t* __restrict__ okey, const uint64_
         ie.ts = t;
         ie.meta = l | ((uint32_t)vl[s] << 8);
         rec[i] = ie;
-        src[i] = s;
         ckey[i] = d;
-        cval[i] = (uint32_t)i;
         atomicAdd(&din[d], 1u);
-    }
-}
-
-// In-edge records in (target, source) order: a gather of the CSR-order records.
-__global__ void in_edge_fill_kernel(const uint32_t* __restrict__ cval, uint64_t m, const InEdge* __restrict__ rec,
-                                    const uint32_t* __restrict__ src, InEdge* __restrict__ in_edge,
-                                    uint32_t* __restrict__ in_p) {
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t e = cval[i];
-        in_edge[i] = rec[e];
-        in_p[i] = src[e];
     }
 }
 
@@ -251,16 +236,35 @@ __global__ void stats_kernel(const uint64_t* __restrict__ off, const uint64_t* _
 }
 
 // Device copy of a caller array that may live in host memory.
+// Large pageable host arrays are page-locked in place for the copy (a DMA
+// straight from the caller's pages instead of the driver's bounce buffers) and
+// released once the stream has consumed them.
 struct Input {
     const void* dptr = nullptr;
     Scratch copy;
+    const void* pinned = nullptr;
+    cudaStream_t stream = nullptr;
     int bind(const void* p, size_t bytes, cudaStream_t s) {
         if (!p) { dptr = nullptr; return TRIPOLL_OK; }
         if (is_device_pointer(p)) { dptr = p; return TRIPOLL_OK; }
         TP_CUDA(copy.alloc(bytes, s));
+        if (bytes >= (size_t(64) << 20)) {
+            if (cudaHostRegister(const_cast<void*>(p), bytes, cudaHostRegisterReadOnly) == cudaSuccess) {
+                pinned = p;
+                stream = s;
+            } else {
+                cudaGetLastError();  // already pinned or not registrable: the plain copy below still works
+            }
+        }
         TP_CUDA(cudaMemcpyAsync(copy.ptr, p, bytes, cudaMemcpyHostToDevice, s));
         dptr = copy.ptr;
         return TRIPOLL_OK;
+    }
+    ~Input() {
+        if (pinned) {
+            cudaStreamSynchronize(stream);
+            cudaHostUnregister(const_cast<void*>(pinned));
+        }
     }
 };
 
@@ -466,11 +470,10 @@ int build_impl(const uint32_t* src_h, const uint32_t* dst_h, const uint32_t* ts_
     TP_CUDA(dalloc(&g->off, n + 1, s));
     TP_CUDA(dalloc(&g->col, m + kColPad, s));
     TP_CUDA(cudaMemsetAsync(g->col + m, 0xFF, kColPad * 4, s));
-    TP_CUDA(dalloc(&g->ts, m, s));
-    if (g->has_el) TP_CUDA(dalloc(&g->el, m, s));
+    TP_CUDA(dalloc(&g->ts, m + kColPad, s));  // padded like col: 16-byte loads of the last quads
+    if (g->has_el) TP_CUDA(dalloc(&g->el, m + kColPad, s));
     TP_CUDA(dalloc(&g->in_off, n + 1, s));
     TP_CUDA(dalloc(&g->in_edge, m, s));
-    TP_CUDA(dalloc(&g->in_p, m, s));
     {
         Scratch ok0, ok1, ov1, cnt, tmp;
         TP_CUDA(ok0.alloc(m * 8, s));
@@ -496,35 +499,30 @@ int build_impl(const uint32_t* src_h, const uint32_t* dst_h, const uint32_t* ts_
         TP_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tb2, kb, vb, m, 0, end_bit, s));
         if (tb2 > tb) TP_CUDA(tmp.alloc(tb2, s));
         TP_CUDA(cub::DeviceRadixSort::SortPairs(tmp.ptr, tb2, kb, vb, m, 0, end_bit, s));
-        // CSR arrays and in-edge records in CSR order; then a stable sort by target
-        Scratch ck0, ck1, cv0, cv1, rec, src;
+        // CSR arrays and in-edge records in CSR order; a stable sort by target then
+        // leaves the records in (target, source) order
+        Scratch ck0, ck1, rec1;
         TP_CUDA(ck0.alloc(m * 4, s));
         TP_CUDA(ck1.alloc(m * 4, s));
-        TP_CUDA(cv0.alloc(m * 4, s));
-        TP_CUDA(cv1.alloc(m * 4, s));
-        TP_CUDA(rec.alloc(m * sizeof(InEdge), s));
-        TP_CUDA(src.alloc(m * 4, s));
+        TP_CUDA(rec1.alloc(m * sizeof(InEdge), s));
         TP_CUDA(cudaMemsetAsync(cnt.ptr, 0, (n + 1) * 4, s));
         if (m)
             csr_fill_kernel<<<grid_for(m), kThreads, 0, s>>>(kb.Current(), vb.Current(), m, b, g->off, g->vl, g->col,
-                                                             g->ts, g->el, rec.as<InEdge>(), src.as<uint32_t>(),
-                                                             ck0.as<uint32_t>(), cv0.as<uint32_t>(),
+                                                             g->ts, g->el, g->in_edge, ck0.as<uint32_t>(),
                                                              cnt.as<uint32_t>()); ::tp::note_launch();
         TP_CUDA(cudaGetLastError());
         ok0.release(); ok1.release(); ov1.release(); uval_d.release();
         TP_CUDA(cub::DeviceScan::ExclusiveSum(tmp.ptr, tb, cnt.as<uint32_t>(), g->in_off, n + 1, s));
         cub::DoubleBuffer<uint32_t> ckb(ck0.as<uint32_t>(), ck1.as<uint32_t>());
-        cub::DoubleBuffer<uint32_t> cvb(cv0.as<uint32_t>(), cv1.as<uint32_t>());
+        cub::DoubleBuffer<InEdge> reb(g->in_edge, rec1.as<InEdge>());
         size_t tb3 = 0;
         const int tbits = std::min(32, b);
-        TP_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tb3, ckb, cvb, m, 0, tbits, s));
+        TP_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tb3, ckb, reb, m, 0, tbits, s));
         Scratch tmp3;
         TP_CUDA(tmp3.alloc(tb3, s));
-        TP_CUDA(cub::DeviceRadixSort::SortPairs(tmp3.ptr, tb3, ckb, cvb, m, 0, tbits, s));
-        if (m)
-            in_edge_fill_kernel<<<grid_for(m), kThreads, 0, s>>>(cvb.Current(), m, rec.as<InEdge>(),
-                                                                 src.as<uint32_t>(), g->in_edge, g->in_p); ::tp::note_launch();
-        TP_CUDA(cudaGetLastError());
+        TP_CUDA(cub::DeviceRadixSort::SortPairs(tmp3.ptr, tb3, ckb, reb, m, 0, tbits, s));
+        if (m && reb.Current() != g->in_edge)
+            TP_CUDA(cudaMemcpyAsync(g->in_edge, reb.Current(), m * sizeof(InEdge), cudaMemcpyDeviceToDevice, s));
     }
     (void)vmask;
 
@@ -562,9 +560,9 @@ int build_impl(const uint32_t* src_h, const uint32_t* dst_h, const uint32_t* ts_
     // 8. the survey plan (work items)
     if ((rc = build_plan(g, s)) != TRIPOLL_OK) return rc;
     TP_CUDA(cudaStreamSynchronize(s));
-    g->info.device_bytes = (n + 1) * 8 * 2 + m * (4 + 4 + (g->has_el ? 1 : 0) + sizeof(InEdge) + 4) +
+    g->info.device_bytes = (n + 1) * 8 * 2 + m * (4 + 4 + (g->has_el ? 1 : 0) + sizeof(InEdge)) +
                            n * (1 + 4 + 4 + (batched ? 4 : 0)) +
-                           (g->n_items_warp + g->n_items_block) * sizeof(WorkItem);
+                           (g->n_items_warp + g->n_items_block + g->n_items_big) * sizeof(WorkItem);
     *out = guard.release();
     return TRIPOLL_OK;
 }
@@ -574,12 +572,12 @@ int build_impl(const uint32_t* src_h, const uint32_t* dst_h, const uint32_t* ts_
 // Arrays return to the pool in the order of the legacy default stream.
 void free_graph_arrays(tripoll_graph* g) {
     void* arrays[] = {g->off, g->col, g->ts, g->el, g->vl, g->deg, g->order, g->graph_of, g->in_off,
-                      g->in_edge, g->in_p, g->items_warp, g->items_block, g->graph_vbase};
+                      g->in_edge, g->items_warp, g->items_block, g->items_big, g->graph_vbase};
     for (void* a : arrays)
         if (a) cudaFreeAsync(a, 0);
     g->off = nullptr; g->col = nullptr; g->ts = nullptr; g->el = nullptr; g->vl = nullptr;
     g->deg = nullptr; g->order = nullptr; g->graph_of = nullptr; g->in_off = nullptr;
-    g->in_edge = nullptr; g->in_p = nullptr; g->items_warp = nullptr; g->items_block = nullptr;
+    g->in_edge = nullptr; g->items_warp = nullptr; g->items_block = nullptr; g->items_big = nullptr;
     g->graph_vbase = nullptr;
 }
 

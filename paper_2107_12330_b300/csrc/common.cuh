@@ -88,7 +88,6 @@ struct GraphDev {
     const uint32_t* graph_of = nullptr; // [n] graph index by position (batched) or null
     const uint64_t* in_off = nullptr;   // [n+1]
     const InEdge* in_edge = nullptr;    // [m]
-    const uint32_t* in_p = nullptr;     // [m] pivot p of each in-edge record
 };
 
 }  // namespace tp
@@ -113,18 +112,18 @@ struct tripoll_graph {
     uint32_t* graph_of = nullptr;
     uint64_t* in_off = nullptr;
     tp::InEdge* in_edge = nullptr;
-    uint32_t* in_p = nullptr;
     // survey plan
-    tp::WorkItem* items_warp = nullptr;
-    tp::WorkItem* items_block = nullptr;
-    uint64_t n_items_warp = 0, n_items_block = 0;
+    tp::WorkItem* items_warp = nullptr;   // d+(q) <= kWarpMaxQ
+    tp::WorkItem* items_block = nullptr;  // kWarpMaxQ < d+(q) <= kBlockChunk
+    tp::WorkItem* items_big = nullptr;    // d+(q) > kBlockChunk, chunks of kBigChunk
+    uint64_t n_items_warp = 0, n_items_block = 0, n_items_big = 0;
     // statistics
     tripoll_graph_info info{};
 
     tp::GraphDev dev() const {
         tp::GraphDev g;
         g.n = n; g.m = m; g.off = off; g.col = col; g.ts = ts; g.el = el; g.vl = vl; g.deg = deg;
-        g.order = order; g.graph_of = graph_of; g.in_off = in_off; g.in_edge = in_edge; g.in_p = in_p;
+        g.order = order; g.graph_of = graph_of; g.in_off = in_off; g.in_edge = in_edge;
         return g;
     }
 };
@@ -133,8 +132,10 @@ namespace tp {
 // survey plan limits shared by the builder and the survey kernels
 constexpr uint32_t kWarpMaxQ = 64;      // middle vertices with d+(q) <= this go to the warp kernel
 constexpr uint32_t kBlockChunk = 1024;  // on-chip staged entries of q's out-list per block item
+constexpr uint32_t kBigChunk = 2048;    // the same for the large-table block kernel
 constexpr uint32_t kWarpInEdges = 64;   // in-edges per warp item
-constexpr uint32_t kBlockInEdges = 256; // in-edges per block item
+constexpr uint32_t kBlockInEdges = 256; // in-edges a block stages at a time
+constexpr uint32_t kItemInEdges = 2048; // in-edges per block item (staged kBlockInEdges at a time)
 constexpr uint32_t kColPad = 8;         // col[] entries past m (0xFFFFFFFF) for 32-byte vector loads
 
 // layout of one survey result record, in words (absent tables: ~0)
@@ -148,7 +149,7 @@ Layout make_layout(uint32_t kinds, uint32_t Lv, uint32_t Le, uint64_t n);
 
 int build_plan(tripoll_graph* g, cudaStream_t s);
 // Launch the survey kernels accumulating into `acc` (zeroed by the caller);
-// counters: device uint32[2] of scratch.
+// counters: device uint32[4] of scratch.
 int launch_survey(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_t t_hi, uint64_t p_lo,
                   uint64_t p_hi, unsigned long long* acc, uint32_t* counters, cudaStream_t s);
 int check_survey_args(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_t t_hi, const void* result);

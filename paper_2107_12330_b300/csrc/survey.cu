@@ -12,11 +12,12 @@
 // per in-edge), the (p,r) edge's (gathered at the hit position), and the
 // (q,r) edge's plus vertex r's (from shared memory).
 //
-// Two kernels split the middle vertices by |Adj+(q)|: a warp-per-item kernel
-// for short out-lists (each warp its own table) and a block-per-item kernel
-// for long ones (tables of up to kBlockChunk entries; longer out-lists are cut
-// into chunks and each in-edge's segment is restricted to the chunk's value
-// range).  Inside an item the in-edges' segments form one flat index space of
+// Three kernels split the middle vertices by |Adj+(q)|: a warp-per-item kernel
+// for short out-lists (each warp its own table), a block-per-item kernel for
+// out-lists of up to kBlockChunk entries, and the same block kernel with
+// tables of kBigChunk entries for longer ones (longer still are cut into
+// chunks and each in-edge's segment is restricted to the chunk's value range
+// by binary search).  Inside an item the in-edges' segments form one flat index space of
 // wedge checks that warps split evenly and walk in chunks of 32 x kUnroll: consecutive lanes
 // read consecutive suffix entries (coalesced), every lane keeps kUnroll
 // independent loads in flight, and no lane idles however skewed the suffix
@@ -76,10 +77,11 @@ struct SurveyArgs {
     uint32_t Lv, Le;
     uint32_t s_words;         // record words mirrored in shared memory (0 for batched graphs)
     uint64_t p_lo, p_hi;      // pivot range
+    uint32_t e_lo, e_hi;      // its CSR positions [off[p_lo], off[p_hi])
     bool restricted;          // pivot range is not all of [0, n)
     Layout lay;
     unsigned long long* out;  // accumulator: one record, or num_graphs records (batched)
-    uint32_t* counters;       // [2] item counters of the two kernels
+    uint32_t* counters;       // [3] item counters of the three kernels
 };
 
 // Home slot of r in a table of `size` slots: a multiplicative hash scaled to size.
@@ -265,10 +267,16 @@ __device__ __forceinline__ uint32_t stage_in_edge(const GraphDev& g, const Surve
     const InEdge ie = g.in_edge[kk];
     bool ok = true;
     if (F & F_TS) ok = in_window(ie.ts, a.t_lo, a.t_hi);  // (p,q) outside the window: no triangle through it
+    // the pivot p owns CSR positions [off[p], off[p+1]): a pivot range is a position range
+    if (a.restricted && (ie.e < a.e_lo || ie.e >= a.e_hi)) ok = false;
     uint32_t p = 0;
-    if (a.restricted || (F & F_EXTRA)) {
-        p = __ldg(&g.in_p[kk]);
-        if (p < a.p_lo || p >= a.p_hi) ok = false;
+    if (F & F_EXTRA) {  // p itself: the last vertex whose out-list starts at or before e
+        uint32_t lo = 0, hi = (uint32_t)g.n - 1;
+        while (lo < hi) {
+            const uint32_t mid = lo + ((hi - lo + 1) >> 1);
+            if (__ldg(&g.off[mid]) <= ie.e) lo = mid; else hi = mid - 1;
+        }
+        p = lo;
     }
     uint32_t j0 = ie.e + 1, jend = ie.end;
     if (ok && chunked && j0 < jend) {
@@ -302,7 +310,8 @@ struct HitQueue {
     uint32_t* pk;
 };
 
-// Fold the first `nq` queued hits, one per lane (nq <= 32).
+// Fold the first `nq` queued hits, one per lane (nq <= 32).  A queue entry is
+// the CSR position of (p,r) and (staged index of r) | (in-edge slot) << 16.
 template <int F, class PosT>
 __device__ __forceinline__ void fold_queue(const GraphDev& g, const SurveyArgs& a, const QTable<PosT>& T,
                                            const InStage& S, const HitQueue& H, uint32_t nq, TriMeta t,
@@ -372,7 +381,7 @@ __device__ __forceinline__ void push_hit(int pos, uint32_t idx, uint32_t k, uint
 template <int F, class PosT>
 __device__ __forceinline__ void scan_flat(const GraphDev& g, const SurveyArgs& a, const QTable<PosT>& T,
                                           const InStage& S, const HitQueue& H, uint32_t n_in, uint32_t f_begin,
-                                          uint32_t f_end, uint32_t q, uint32_t l_q, uint32_t d_q,
+                                          uint32_t f_end, uint32_t qbase, uint32_t q, uint32_t l_q, uint32_t d_q,
                                           unsigned long long* s_tab, unsigned long long* grec,
                                           unsigned long long& cnt) {
     const uint32_t lane = threadIdx.x & 31;
@@ -454,33 +463,34 @@ __device__ void flush_count(unsigned long long cnt, const SurveyArgs& a, unsigne
 
 // ---- block kernel: one item per block at a time ---------------------------------------------
 
-constexpr uint32_t kBlockTable = 3 * kBlockChunk;
-
-// dynamic shared memory of the block kernel after the record mirror
-// dynamic shared memory of the block kernel after the record mirror (the
-// degree array of staged entries only for kinds that use degrees)
-template <int F>
+// dynamic shared memory of the block kernel after the record mirror, for
+// staged parts of up to CHUNK entries in a table of 3*CHUNK slots (the degree
+// array of staged entries only for kinds that use degrees)
+template <int F, uint32_t CHUNK>
 constexpr size_t block_smem_fixed() {
-    return kWarps * kHitQ * 8 + kBlockTable * 4 + kBlockChunk * 4 * ((F & F_EXTRA) ? 2 : 1) + kBlockTable * 2 +
-           kBlockChunk * 2 + kBlockInEdges * 4 * 5 + (kBlockInEdges + 1) * 4;
+    return kWarps * kHitQ * 8 + 3 * CHUNK * 4 + CHUNK * 4 * ((F & F_EXTRA) ? 2 : 1) + 3 * CHUNK * 2 + CHUNK * 2 +
+           kBlockInEdges * 4 * 5 + (kBlockInEdges + 1) * 4;
 }
 
-template <int F>
-__global__ void __launch_bounds__(kBlockThreads) survey_block_kernel(GraphDev g, const WorkItem* __restrict__ items,
+// CTR selects the item counter: 1 for the kBlockChunk list, 2 for the kBigChunk list.
+template <int F, uint32_t CHUNK, int CTR>
+__global__ void __launch_bounds__(kBlockThreads, CHUNK <= kBlockChunk ? 5 : 3)
+    survey_block_kernel(GraphDev g, const WorkItem* __restrict__ items,
                                                                      uint32_t n_items, SurveyArgs a) {
+    constexpr uint32_t kBlockTable = 3 * CHUNK;
     extern __shared__ __align__(16) unsigned char smem[];
     using BlockScan = cub::BlockScan<uint32_t, kBlockThreads>;
     __shared__ typename BlockScan::TempStorage scan_tmp;
     __shared__ uint32_t s_item, s_total;
 
     unsigned long long* s_tab = reinterpret_cast<unsigned long long*>(smem);
-    unsigned char* base = smem + a.s_words * 8;
+    unsigned char* base = smem + ((a.s_words * 8 + 15) & ~15u);
     QTable<uint16_t> T;
     T.key = reinterpret_cast<uint32_t*>(base);
     T.ts = T.key + kBlockTable;
-    T.deg = T.ts + kBlockChunk;  // present only with F_EXTRA
+    T.deg = T.ts + CHUNK;  // present only with F_EXTRA
     InStage S;
-    S.j0 = T.deg + ((F & F_EXTRA) ? kBlockChunk : 0);
+    S.j0 = T.deg + ((F & F_EXTRA) ? CHUNK : 0);
     S.jend = S.j0 + kBlockInEdges;
     S.tpq = S.jend + kBlockInEdges;
     S.meta = S.tpq + kBlockInEdges;
@@ -492,17 +502,17 @@ __global__ void __launch_bounds__(kBlockThreads) survey_block_kernel(GraphDev g,
     H.pk = H.idx + kHitQ;
     T.pos = reinterpret_cast<uint16_t*>(hq + kWarps * 2 * kHitQ);
     T.el = reinterpret_cast<uint8_t*>(T.pos + kBlockTable);
-    T.vl = T.el + kBlockChunk;
+    T.vl = T.el + CHUNK;
 
     for (uint32_t w = threadIdx.x; w < a.s_words; w += blockDim.x) s_tab[w] = 0;
     unsigned long long cnt = 0;
     unsigned long long* grec_prev = nullptr;
 
     while (true) {
-        if (threadIdx.x == 0) s_item = atomicAdd(&a.counters[1], 1u);
+        if (threadIdx.x == 0) s_item = atomicAdd(&a.counters[CTR], 1u);
         __syncthreads();  // also: the previous item's table and stage are no longer read
-        const uint32_t it = s_item;
-        if (it >= n_items) break;
+        if (s_item >= n_items) break;
+        const uint32_t it = n_items - 1 - s_item;  // high positions first: the hubs' long items start early
         const WorkItem item = items[it];
         const uint32_t q = item.q;
         unsigned long long* grec = record_of(g, a, q);
@@ -521,21 +531,24 @@ __global__ void __launch_bounds__(kBlockThreads) survey_block_kernel(GraphDev g,
         const bool chunked = item.flags & 1u;
         const uint32_t vlo = chunked ? __ldg(&g.col[qbase]) : 0u;
         const uint32_t vhi = chunked ? __ldg(&g.col[qbase + len - 1]) : 0xFFFFFFFFu;
-        const uint32_t n_in = item.in_hi - item.in_lo;
-        uint32_t np = 0;
-        if (threadIdx.x < n_in) np = stage_in_edge<F>(g, a, S, threadIdx.x, item.in_lo + threadIdx.x, chunked, vlo, vhi);
-        uint32_t pre, total;
-        BlockScan(scan_tmp).ExclusiveSum(np, pre, total);
-        if (threadIdx.x < n_in) S.pp[threadIdx.x] = pre;
-        if (threadIdx.x == 0) { S.pp[n_in] = total; s_total = total; }
-        __syncthreads();
         const uint32_t l_q = (F & F_VL) ? __ldg(&g.vl[q]) : 0u;
         const uint32_t d_q = (F & F_EXTRA) ? __ldg(&g.deg[q]) : 0u;
         const uint32_t warp = threadIdx.x >> 5;
-        const uint32_t f_begin = (uint32_t)(((uint64_t)s_total * warp) / kWarps);
-        const uint32_t f_end = (uint32_t)(((uint64_t)s_total * (warp + 1)) / kWarps);
-        scan_flat<F>(g, a, T, S, H, n_in, f_begin, f_end, q, l_q, d_q, s_tab,
-                     grec, cnt);
+        // the table stays; the item's in-edges are staged and scanned kBlockInEdges at a time
+        for (uint32_t g0 = item.in_lo; g0 < item.in_hi; g0 += kBlockInEdges) {
+            if (g0 != item.in_lo) __syncthreads();  // the previous group's stage is no longer read
+            const uint32_t n_in = min(kBlockInEdges, item.in_hi - g0);
+            uint32_t np = 0;
+            if (threadIdx.x < n_in) np = stage_in_edge<F>(g, a, S, threadIdx.x, g0 + threadIdx.x, chunked, vlo, vhi);
+            uint32_t pre, total;
+            BlockScan(scan_tmp).ExclusiveSum(np, pre, total);
+            if (threadIdx.x < n_in) S.pp[threadIdx.x] = pre;
+            if (threadIdx.x == 0) { S.pp[n_in] = total; s_total = total; }
+            __syncthreads();
+            const uint32_t f_begin = (uint32_t)(((uint64_t)s_total * warp) / kWarps);
+            const uint32_t f_end = (uint32_t)(((uint64_t)s_total * (warp + 1)) / kWarps);
+            scan_flat<F>(g, a, T, S, H, n_in, f_begin, f_end, qbase, q, l_q, d_q, s_tab, grec, cnt);
+        }
     }
     if (grec_prev) flush_count(cnt, a, s_tab, grec_prev);
     __syncthreads();
@@ -545,7 +558,7 @@ __global__ void __launch_bounds__(kBlockThreads) survey_block_kernel(GraphDev g,
 // ---- warp kernel: one item per warp at a time ------------------------------------------------
 
 constexpr uint32_t kWTable = 3 * kWarpMaxQ;
-struct WarpSmem {
+struct __align__(16) WarpSmem {
     uint32_t key[kWTable];
     uint32_t ts[kWarpMaxQ];
     uint32_t deg[kWarpMaxQ];
@@ -617,7 +630,7 @@ __global__ void __launch_bounds__(kBlockThreads) survey_warp_kernel(GraphDev g, 
         HitQueue H;
         H.idx = ws.qidx;
         H.pk = ws.qpk;
-        scan_flat<F>(g, a, T, S, H, n_in, 0, total, q, l_q, d_q, s_tab, grec, cnt);
+        scan_flat<F>(g, a, T, S, H, n_in, 0, total, qbase, q, l_q, d_q, s_tab, grec, cnt);
     }
     if (grec_prev) flush_count(cnt, a, s_tab, grec_prev);
     __syncthreads();
@@ -628,55 +641,56 @@ __global__ void __launch_bounds__(kBlockThreads) survey_warp_kernel(GraphDev g, 
 
 __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
 
+// Items of middle vertex q: for each part of Adj+(q) staged at once (one part
+// unless d+(q) exceeds the kernel's chunk), groups of at most `per` in-edges.
+__device__ __forceinline__ void plan_shape(uint64_t dp, uint64_t di, int& kind, uint64_t& chunk, uint64_t& per) {
+    kind = dp <= kWarpMaxQ ? 0 : (dp <= 4 * kBlockChunk ? 1 : 2);
+    chunk = kind == 0 ? kWarpMaxQ : (kind == 1 ? kBlockChunk : kBigChunk);
+    per = kind == 0 ? kWarpInEdges : kItemInEdges;
+}
+
 __global__ void plan_count_kernel(const uint64_t* __restrict__ off, const uint64_t* __restrict__ in_off, uint64_t n,
-                                  uint32_t* __restrict__ cw, uint32_t* __restrict__ cb) {
+                                  uint32_t* __restrict__ c0, uint32_t* __restrict__ c1, uint32_t* __restrict__ c2) {
     for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < n; q += (uint64_t)gridDim.x * blockDim.x) {
-        uint64_t dp = off[q + 1] - off[q], di = in_off[q + 1] - in_off[q];
-        uint32_t w = 0, b = 0;
+        const uint64_t dp = off[q + 1] - off[q], di = in_off[q + 1] - in_off[q];
+        uint32_t cnt[3] = {0, 0, 0};
         if (dp > 0 && di > 0) {
-            if (dp <= kWarpMaxQ) {
-                w = (uint32_t)((di + kWarpInEdges - 1) / kWarpInEdges);
-            } else {
-                uint64_t chunks = (dp + kBlockChunk - 1) / kBlockChunk;
-                uint64_t groups = (di + kBlockInEdges - 1) / kBlockInEdges;
-                b = (uint32_t)(chunks * groups);
-            }
+            int kind;
+            uint64_t chunk, per;
+            plan_shape(dp, di, kind, chunk, per);
+            cnt[kind] = (uint32_t)(((dp + chunk - 1) / chunk) * ((di + per - 1) / per));
         }
-        cw[q] = w;
-        cb[q] = b;
+        c0[q] = cnt[0];
+        c1[q] = cnt[1];
+        c2[q] = cnt[2];
     }
 }
 
 __global__ void plan_fill_kernel(const uint64_t* __restrict__ off, const uint64_t* __restrict__ in_off, uint64_t n,
-                                 const uint32_t* __restrict__ ow, const uint32_t* __restrict__ ob,
-                                 WorkItem* __restrict__ iw, WorkItem* __restrict__ ib) {
+                                 const uint32_t* __restrict__ o0, const uint32_t* __restrict__ o1,
+                                 const uint32_t* __restrict__ o2, WorkItem* __restrict__ i0, WorkItem* __restrict__ i1,
+                                 WorkItem* __restrict__ i2) {
     for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < n; q += (uint64_t)gridDim.x * blockDim.x) {
-        uint64_t dp = off[q + 1] - off[q], di = in_off[q + 1] - in_off[q];
+        const uint64_t dp = off[q + 1] - off[q], di = in_off[q + 1] - in_off[q];
         if (dp == 0 || di == 0) continue;
+        int kind;
+        uint64_t chunk, per;
+        plan_shape(dp, di, kind, chunk, per);
+        WorkItem* dst = kind == 0 ? i0 : (kind == 1 ? i1 : i2);
+        uint32_t o = kind == 0 ? o0[q] : (kind == 1 ? o1[q] : o2[q]);
         const uint32_t ilo = (uint32_t)in_off[q];
-        if (dp <= kWarpMaxQ) {
-            uint32_t o = ow[q];
-            for (uint64_t s = 0; s < di; s += kWarpInEdges) {
+        const bool chunked = dp > chunk;
+        for (uint64_t c = 0; c < dp; c += chunk) {
+            for (uint64_t s = 0; s < di; s += per) {
                 WorkItem it;
-                it.q = (uint32_t)q; it.qlo = 0; it.qlen = (uint32_t)dp;
+                it.q = (uint32_t)q;
+                it.qlo = (uint32_t)c;
+                it.qlen = (uint32_t)umin64(chunk, dp - c);
                 it.in_lo = ilo + (uint32_t)s;
-                it.in_hi = ilo + (uint32_t)umin64(di, s + kWarpInEdges);
-                it.flags = 0; it.pad0 = it.pad1 = 0;
-                iw[o++] = it;
-            }
-        } else {
-            uint32_t o = ob[q];
-            const bool chunked = dp > kBlockChunk;
-            for (uint64_t c = 0; c < dp; c += kBlockChunk) {
-                for (uint64_t s = 0; s < di; s += kBlockInEdges) {
-                    WorkItem it;
-                    it.q = (uint32_t)q; it.qlo = (uint32_t)c;
-                    it.qlen = (uint32_t)umin64(kBlockChunk, dp - c);
-                    it.in_lo = ilo + (uint32_t)s;
-                    it.in_hi = ilo + (uint32_t)umin64(di, s + kBlockInEdges);
-                    it.flags = chunked ? 1u : 0u; it.pad0 = it.pad1 = 0;
-                    ib[o++] = it;
-                }
+                it.in_hi = ilo + (uint32_t)umin64(di, s + per);
+                it.flags = chunked ? 1u : 0u;
+                it.pad0 = it.pad1 = 0;
+                dst[o++] = it;
             }
         }
     }
@@ -687,18 +701,29 @@ unsigned grid_n(uint64_t items) {
     return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(b, 148u * 64u));
 }
 
-// Resident blocks per SM of a kernel at a dynamic shared-memory size, with the
-// kernel's shared-memory limit raised once; cached per (kernel, size, device).
+// Resident blocks per SM of a kernel at a dynamic shared-memory size; cached
+// per (kernel, size, device).  The kernel's dynamic shared-memory limit is
+// raised once per (kernel, device) to the device's opt-in maximum, so launches
+// of any size up to it stay valid whatever size was queried first.
 int blocks_per_sm(const void* kernel, size_t smem) {
     static std::mutex mu;
     static std::map<std::tuple<const void*, size_t, int>, int> cache;
+    static std::map<std::pair<const void*, int>, bool> raised;
     int dev = 0;
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lk(mu);
     auto key = std::make_tuple(kernel, smem, dev);
     auto it = cache.find(key);
     if (it != cache.end()) return it->second;
-    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (!raised[std::make_pair(kernel, dev)]) {
+        int optin = 0;
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        int static_bytes = 0;
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, kernel) == cudaSuccess) static_bytes = (int)fa.sharedSizeBytes;
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - static_bytes);
+        raised[std::make_pair(kernel, dev)] = true;
+    }
     int per = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kBlockThreads, smem);
     per = std::max(per, 1);
@@ -718,12 +743,18 @@ void launch_f(const tripoll_graph* g, const SurveyArgs& a, cudaStream_t s, int s
                                                                          (uint32_t)g->n_items_warp, a); ::tp::note_launch();
     }
     if (g->n_items_block) {
-        size_t sm = a.s_words * 8 + block_smem_fixed<F>();
-        const int per = blocks_per_sm((const void*)survey_block_kernel<F>, sm);
-        uint64_t blocks = (uint64_t)per * sms;
-        blocks = std::min<uint64_t>(blocks, g->n_items_block);
-        survey_block_kernel<F><<<(unsigned)blocks, kBlockThreads, sm, s>>>(gd, g->items_block,
-                                                                          (uint32_t)g->n_items_block, a); ::tp::note_launch();
+        size_t sm = ((a.s_words * 8 + 15) & ~15u) + block_smem_fixed<F, kBlockChunk>();
+        const int per = blocks_per_sm((const void*)survey_block_kernel<F, kBlockChunk, 1>, sm);
+        uint64_t blocks = std::min<uint64_t>((uint64_t)per * sms, g->n_items_block);
+        survey_block_kernel<F, kBlockChunk, 1><<<(unsigned)blocks, kBlockThreads, sm, s>>>(
+            gd, g->items_block, (uint32_t)g->n_items_block, a); ::tp::note_launch();
+    }
+    if (g->n_items_big) {
+        size_t sm = ((a.s_words * 8 + 15) & ~15u) + block_smem_fixed<F, kBigChunk>();
+        const int per = blocks_per_sm((const void*)survey_block_kernel<F, kBigChunk, 2>, sm);
+        uint64_t blocks = std::min<uint64_t>((uint64_t)per * sms, g->n_items_big);
+        survey_block_kernel<F, kBigChunk, 2><<<(unsigned)blocks, kBlockThreads, sm, s>>>(
+            gd, g->items_big, (uint32_t)g->n_items_big, a); ::tp::note_launch();
     }
 }
 
@@ -737,31 +768,35 @@ constexpr LaunchFn kLaunch[16] = {&launch_f<0>,  &launch_f<1>,  &launch_f<2>,  &
 
 int build_plan(tripoll_graph* g, cudaStream_t s) {
     const uint64_t n = g->n;
-    Scratch cw, cb, ow, ob, tmp;
-    TP_CUDA(cw.alloc((n + 1) * 4, s));
-    TP_CUDA(cb.alloc((n + 1) * 4, s));
-    TP_CUDA(ow.alloc((n + 1) * 4, s));
-    TP_CUDA(ob.alloc((n + 1) * 4, s));
-    TP_CUDA(cudaMemsetAsync(cw.ptr, 0, (n + 1) * 4, s));
-    TP_CUDA(cudaMemsetAsync(cb.ptr, 0, (n + 1) * 4, s));
-    if (n) plan_count_kernel<<<grid_n(n), 256, 0, s>>>(g->off, g->in_off, n, cw.as<uint32_t>(), cb.as<uint32_t>()); ::tp::note_launch();
+    Scratch c[3], o[3], tmp;
+    for (int k = 0; k < 3; ++k) {
+        TP_CUDA(c[k].alloc((n + 1) * 4, s));
+        TP_CUDA(o[k].alloc((n + 1) * 4, s));
+        TP_CUDA(cudaMemsetAsync(c[k].ptr, 0, (n + 1) * 4, s));
+    }
+    if (n)
+        plan_count_kernel<<<grid_n(n), 256, 0, s>>>(g->off, g->in_off, n, c[0].as<uint32_t>(), c[1].as<uint32_t>(),
+                                                    c[2].as<uint32_t>()); ::tp::note_launch();
     TP_CUDA(cudaGetLastError());
     size_t tb = 0;
-    TP_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tb, cw.as<uint32_t>(), ow.as<uint32_t>(), n + 1, s));
+    TP_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tb, c[0].as<uint32_t>(), o[0].as<uint32_t>(), n + 1, s));
     TP_CUDA(tmp.alloc(tb, s));
-    TP_CUDA(cub::DeviceScan::ExclusiveSum(tmp.ptr, tb, cw.as<uint32_t>(), ow.as<uint32_t>(), n + 1, s));
-    TP_CUDA(cub::DeviceScan::ExclusiveSum(tmp.ptr, tb, cb.as<uint32_t>(), ob.as<uint32_t>(), n + 1, s));
-    uint32_t tot[2] = {0, 0};
-    TP_CUDA(cudaMemcpyAsync(&tot[0], ow.as<uint32_t>() + n, 4, cudaMemcpyDeviceToHost, s));
-    TP_CUDA(cudaMemcpyAsync(&tot[1], ob.as<uint32_t>() + n, 4, cudaMemcpyDeviceToHost, s));
+    uint32_t tot[3] = {0, 0, 0};
+    for (int k = 0; k < 3; ++k) {
+        TP_CUDA(cub::DeviceScan::ExclusiveSum(tmp.ptr, tb, c[k].as<uint32_t>(), o[k].as<uint32_t>(), n + 1, s));
+        TP_CUDA(cudaMemcpyAsync(&tot[k], o[k].as<uint32_t>() + n, 4, cudaMemcpyDeviceToHost, s));
+    }
     TP_CUDA(cudaStreamSynchronize(s));
     g->n_items_warp = tot[0];
     g->n_items_block = tot[1];
+    g->n_items_big = tot[2];
     TP_CUDA(cudaMallocAsync((void**)&g->items_warp, std::max<uint64_t>(1, tot[0]) * sizeof(WorkItem), s));
     TP_CUDA(cudaMallocAsync((void**)&g->items_block, std::max<uint64_t>(1, tot[1]) * sizeof(WorkItem), s));
+    TP_CUDA(cudaMallocAsync((void**)&g->items_big, std::max<uint64_t>(1, tot[2]) * sizeof(WorkItem), s));
     if (n)
-        plan_fill_kernel<<<grid_n(n), 256, 0, s>>>(g->off, g->in_off, n, ow.as<uint32_t>(), ob.as<uint32_t>(),
-                                                   g->items_warp, g->items_block); ::tp::note_launch();
+        plan_fill_kernel<<<grid_n(n), 256, 0, s>>>(g->off, g->in_off, n, o[0].as<uint32_t>(), o[1].as<uint32_t>(),
+                                                   o[2].as<uint32_t>(), g->items_warp, g->items_block,
+                                                   g->items_big); ::tp::note_launch();
     TP_CUDA(cudaGetLastError());
     return TRIPOLL_OK;
 }
@@ -779,6 +814,16 @@ int launch_survey(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_
     a.p_lo = p_lo;
     a.p_hi = p_hi;
     a.restricted = !(p_lo == 0 && p_hi >= g->n);
+    a.e_lo = 0;
+    a.e_hi = (uint32_t)g->m;
+    if (a.restricted) {  // two offsets of the pivot range, read once on the host
+        uint64_t ends[2] = {0, 0};
+        TP_CUDA(cudaMemcpyAsync(&ends[0], g->off + p_lo, 8, cudaMemcpyDeviceToHost, s));
+        TP_CUDA(cudaMemcpyAsync(&ends[1], g->off + p_hi, 8, cudaMemcpyDeviceToHost, s));
+        TP_CUDA(cudaStreamSynchronize(s));
+        a.e_lo = (uint32_t)ends[0];
+        a.e_hi = (uint32_t)ends[1];
+    }
     a.lay = lay;
     a.out = acc;
     a.counters = counters;
@@ -795,7 +840,7 @@ int launch_survey(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_
         F |= F_EXTRA | F_TS;
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
-    TP_CUDA(cudaMemsetAsync(counters, 0, 8, s));
+    TP_CUDA(cudaMemsetAsync(counters, 0, 16, s));
     kLaunch[F](g, a, s, sms);
     TP_CUDA(cudaGetLastError());
     return TRIPOLL_OK;

@@ -231,7 +231,7 @@ def serving_graph(i: int) -> Graph:
                       name=f"serve{i}_rmat{scales[i]}")
 
 
-def chung_lu_50m(m_samples: int = 1_400_000_000, n: int = 50_000_000) -> Graph:
+def chung_lu_50m(m_samples: int = 1_200_000_000, n: int = 50_000_000) -> Graph:
     """Chung-Lu exponent 2.1 at 50M vertices; ts = Poisson arrivals over 3.15e8 s;
     vertex labels Zipf(1.1) over {0..63}; edge labels uniform {0..7}; full survey."""
     seed = 3

@@ -48,6 +48,33 @@ def test_full_size_survey_matches_stored_oracle(name, make):
     assert bad.size == 0, f"words {bad[:10].tolist()} differ: gpu {got[bad[:10]].tolist()} oracle {want[bad[:10]].tolist()}"
 
 
+def test_chung_lu_recipe_matches_stored_oracle():
+    """The 50M-vertex Chung-Lu recipe (exponent 2.1, heavy hubs, 64 vertex labels) at
+    2M vertices: all four tables, against the oracle's digest and small tables."""
+    import hashlib
+    import torch
+    gold = _golden("chunglu2m")
+    g = synth.chung_lu_50m(m_samples=gold["m_in"], n=gold["n"])
+    dev = [torch.from_numpy(x).cuda() for x in (g.src, g.dst, g.ts, g.elabel, g.vlabel)]
+    h = tp.tripoll_graph_create(*dev, g.n, g.num_vlabels, g.num_elabels)
+    try:
+        st = tp.tripoll_graph_stats(h)
+        w = tp.tripoll_result_words(g.kinds, g.num_vlabels, g.num_elabels, g.n)
+        assert w == gold["words"]
+        out = torch.zeros(w, dtype=torch.int64, device="cuda")
+        tp.tripoll_survey(h, g.kinds, 0, 0xFFFFFFFF, out)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().view(np.uint64)
+    finally:
+        tp.tripoll_destroy(h)
+    assert st["num_edges"] == gold["stats"]["m"] and st["wedges"] == gold["stats"]["wedges"]
+    parts = tp.split_result(got, g.kinds, g.num_vlabels, g.num_elabels)
+    assert int(parts["count"][0]) == gold["count"]
+    assert parts["hist"].tolist() == gold["hist"]
+    assert parts["etri"].tolist() == gold["etri"]
+    assert hashlib.sha256(got.astype("<u8").tobytes()).hexdigest() == gold["sha256"]
+
+
 def test_full_batched_family_matches_stored_oracle():
     """All 20,000 graphs of the batched family in one build and one survey launch
     pair: per-graph records against the oracle's, by SHA-256 of the whole result

@@ -1,0 +1,93 @@
+"""Serving: resident graphs and continuously batched requests.  Every result a
+request gets in a mix of concurrent requests (different graphs, kinds and
+windows, submitted from several threads while others run) must equal the
+survey of that request alone, bit for bit."""
+import threading
+
+import numpy as np
+import pytest
+
+import synth
+import paper_2107_12330_b300 as tp
+
+pytestmark = pytest.mark.gpu
+KINDS = [tp.TRIPOLL_COUNT, tp.TRIPOLL_CLOSURE_HIST, tp.TRIPOLL_VLABEL_TRIPLES, tp.TRIPOLL_ELABEL_TRIPLES,
+         tp.TRIPOLL_COUNT | tp.TRIPOLL_CLOSURE_HIST | tp.TRIPOLL_ELABEL_TRIPLES]
+
+
+def _graphs():
+    out = []
+    for i, sc in enumerate([10, 12, 14]):
+        g = synth.rmat_graph(sc, 16, i + 1, ts_bits=24, num_vlabels=16, num_elabels=8)
+        h = tp.tripoll_graph_create(g.src, g.dst, g.ts, g.elabel, g.vlabel, g.n, 16, 8)
+        out.append((g, h))
+    return out
+
+
+def test_requests_in_a_mix_equal_requests_alone():
+    graphs = _graphs()
+    try:
+        reqs = []
+        for i in range(60):
+            d = [synth.draw(5, 9, 4 * i + j) for j in range(4)]
+            gi = d[0] % len(graphs)
+            k = KINDS[d[1] % len(KINDS)]
+            lo, hi = sorted(((d[2] >> 40) % (1 << 24), (d[3] >> 40) % (1 << 24)))
+            if i % 7 == 0:
+                lo, hi = 0, 0xFFFFFFFF
+            reqs.append((gi, k, lo, hi))
+        alone = []
+        for gi, k, lo, hi in reqs:
+            g, h = graphs[gi]
+            o = np.zeros(tp.tripoll_result_words(k, 16, 8, g.n), np.uint64)
+            tp.tripoll_survey(h, k, lo, hi, o)
+            alone.append(o)
+        srv = tp.tripoll_server_create(1 << 30, 8)
+        try:
+            slots = [tp.tripoll_server_add_graph(srv, h) for _, h in graphs]
+            ids = [None] * len(reqs)
+
+            def submit(part):
+                for i in part:
+                    gi, k, lo, hi = reqs[i]
+                    ids[i] = tp.tripoll_server_submit(srv, slots[gi], k, lo, hi)
+
+            threads = [threading.Thread(target=submit, args=(range(t, len(reqs), 3),)) for t in range(3)]
+            for t in threads:
+                t.start()
+            for t in threads:
+                t.join()
+            for i, (gi, k, lo, hi) in enumerate(reqs):
+                g, _ = graphs[gi]
+                o = np.zeros(tp.tripoll_result_words(k, 16, 8, g.n), np.uint64)
+                lat = tp.tripoll_server_wait(srv, ids[i], o, 120000)
+                assert lat > 0
+                assert np.array_equal(o, alone[i]), f"request {i} differs in the mix"
+            with pytest.raises(tp.TripollError) as e:
+                tp.tripoll_server_wait(srv, 10 ** 9, None, 10)
+            assert e.value.status == tp.TRIPOLL_ERR_NOT_FOUND
+        finally:
+            tp.tripoll_server_destroy(srv)
+    finally:
+        for _, h in graphs:
+            tp.tripoll_destroy(h)
+
+
+def test_requests_beyond_the_scratch_budget_are_refused():
+    graphs = _graphs()
+    try:
+        srv = tp.tripoll_server_create(1024, 4)  # 1 KB of scratch: a 33-word histogram fits, 4096 triples do not
+        try:
+            slot = tp.tripoll_server_add_graph(srv, graphs[0][1])
+            rid = tp.tripoll_server_submit(srv, slot, tp.TRIPOLL_CLOSURE_HIST)
+            o = np.zeros(33, np.uint64)
+            tp.tripoll_server_wait(srv, rid, o, 60000)
+            assert o.sum() > 0
+            with pytest.raises(tp.TripollError) as e:
+                tp.tripoll_server_submit(srv, slot, tp.TRIPOLL_VLABEL_TRIPLES)
+            assert e.value.status == tp.TRIPOLL_ERR_NO_MEMORY
+        finally:
+            tp.tripoll_server_destroy(srv)
+    finally:
+        for _, h in graphs:
+            tp.tripoll_destroy(h)
