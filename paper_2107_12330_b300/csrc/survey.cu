@@ -194,7 +194,12 @@ struct QTable {
     uint32_t size;  // slots: 3 per staged entry (load factor <= 1/3)
 };
 
-__device__ __forceinline__ uint32_t table_size(uint32_t len) { return max(3u * len, 4u); }
+#ifndef TP_TABLE_FACTOR
+#define TP_TABLE_FACTOR 3
+#endif
+constexpr uint32_t kTableFactor = TP_TABLE_FACTOR;  // table slots per staged entry
+
+__device__ __forceinline__ uint32_t table_size(uint32_t len) { return max(kTableFactor * len, 4u); }
 
 // Insert the entries [i0, len) step `stride` of the staged out-list part at
 // CSR position qbase; entries whose (q,r) timestamp lies outside the window
@@ -226,6 +231,16 @@ __device__ __forceinline__ void table_fill(const GraphDev& g, const SurveyArgs& 
 template <class PosT>
 __device__ __forceinline__ int table_find(const QTable<PosT>& T, uint32_t r) {
     uint32_t h = hash_slot(r, T.size);
+#ifdef TP_PROBE2
+    // the home slot and the next one are read together; most searches end there
+    uint32_t h1 = h + 1 == T.size ? 0u : h + 1;
+    const uint32_t k0 = T.key[h], k1 = T.key[h1];
+    if (k0 == r) return (int)T.pos[h];
+    if (k0 == kEmpty) return -1;
+    if (k1 == r) return (int)T.pos[h1];
+    if (k1 == kEmpty) return -1;
+    h = h1 + 1 == T.size ? 0u : h1 + 1;
+#endif
     while (true) {
         const uint32_t key = T.key[h];
         if (key == r) return (int)T.pos[h];
@@ -300,8 +315,11 @@ __device__ __forceinline__ uint32_t seg_of(const uint32_t* pp, uint32_t lo, uint
     return lo;
 }
 
-constexpr int kUnroll = 2;  // quads each lane has in flight per chunk (8 positions)
-constexpr int kHitQ = 64;   // per-warp queue of hits awaiting the fold
+#ifndef TP_UNROLL
+#define TP_UNROLL 2
+#endif
+constexpr int kUnroll = TP_UNROLL;  // quads each lane has in flight per chunk
+constexpr int kHitQ = 160;  // per-warp queue of hits awaiting the fold (< 32 left + 4 x 32 new)
 
 // Per-warp queue of wedge checks that hit: CSR position of (p,r), and
 // (staged index of r) | (in-edge slot) << 16.
@@ -310,17 +328,17 @@ struct HitQueue {
     uint32_t* pk;
 };
 
-// Fold the first `nq` queued hits, one per lane (nq <= 32).  A queue entry is
+// Fold the `nq` queued hits from entry `head` on, one per lane (nq <= 32).  A queue entry is
 // the CSR position of (p,r) and (staged index of r) | (in-edge slot) << 16.
 template <int F, class PosT>
 __device__ __forceinline__ void fold_queue(const GraphDev& g, const SurveyArgs& a, const QTable<PosT>& T,
-                                           const InStage& S, const HitQueue& H, uint32_t nq, TriMeta t,
+                                           const InStage& S, const HitQueue& H, uint32_t head, uint32_t nq, TriMeta t,
                                            unsigned long long* s_tab, unsigned long long* grec,
                                            unsigned long long& cnt) {
     const uint32_t lane = threadIdx.x & 31;
     bool keep = lane < nq;
     if (keep) {
-        const uint32_t idx = H.idx[lane], pk = H.pk[lane];
+        const uint32_t idx = H.idx[head + lane], pk = H.pk[head + lane];
         const uint32_t pos = pk & 0xffffu, k = pk >> 16;
         t.t_pq = S.tpq[k];
         const uint32_t meta = S.meta[k];
@@ -343,33 +361,51 @@ __device__ __forceinline__ void fold_queue(const GraphDev& g, const SurveyArgs& 
     fold_warp<F>(keep, t, a, s_tab, grec, cnt, g.order);
 }
 
-// Queue this lane's hit (pos >= 0) at CSR position idx of slot k; fold the
-// queue when 32 hits are waiting.  Called by the whole warp.
+// Queue the hits of this lane's quad -- pos[i] >= 0 for a hit at CSR position
+// e0 + i of in-edge slot k -- with one ballot per quad position, and fold the
+// queue 32 entries at a time while 32 or more are waiting.  Called by the
+// whole warp; nq (< 32 on entry and exit) is warp-uniform.
 template <int F, class PosT>
-__device__ __forceinline__ void push_hit(int pos, uint32_t idx, uint32_t k, uint32_t& nq, const GraphDev& g,
-                                         const SurveyArgs& a, const QTable<PosT>& T, const InStage& S,
-                                         const HitQueue& H, const TriMeta& t, unsigned long long* s_tab,
-                                         unsigned long long* grec, unsigned long long& cnt) {
+__device__ __forceinline__ void push_quad(const int (&pos)[4], uint32_t e0, uint32_t k, uint32_t& nq,
+                                          const GraphDev& g, const SurveyArgs& a, const QTable<PosT>& T,
+                                          const InStage& S, const HitQueue& H, const TriMeta& t,
+                                          unsigned long long* s_tab, unsigned long long* grec,
+                                          unsigned long long& cnt) {
     const uint32_t lane = threadIdx.x & 31;
-    const unsigned hm = __ballot_sync(0xffffffffu, pos >= 0);
-    if (!hm) return;
-    if (pos >= 0) {
-        const uint32_t slot = nq + __popc(hm & ((1u << lane) - 1u));
-        H.idx[slot] = idx;
-        H.pk[slot] = (uint32_t)pos | (k << 16);
-    }
-    nq += __popc(hm);
-    if (nq >= 32) {
-        __syncwarp();
-        fold_queue<F>(g, a, T, S, H, 32, t, s_tab, grec, cnt);
-        __syncwarp();
-        nq -= 32;
-        if (lane < nq) {
-            H.idx[lane] = H.idx[32 + lane];
-            H.pk[lane] = H.pk[32 + lane];
+    const uint32_t lt = (1u << lane) - 1u;
+    unsigned b[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) b[i] = __ballot_sync(0xffffffffu, pos[i] >= 0);
+    if (!(b[0] | b[1] | b[2] | b[3])) return;
+    uint32_t off = nq;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        if (pos[i] >= 0) {
+            const uint32_t slot = off + __popc(b[i] & lt);
+            H.idx[slot] = e0 + i;
+            H.pk[slot] = (uint32_t)pos[i] | (k << 16);
         }
-        __syncwarp();
+        off += __popc(b[i]);
     }
+    nq = off;
+    if (nq < 32) return;
+    __syncwarp();
+    uint32_t head = 0;
+    for (; nq - head >= 32; head += 32) fold_queue<F>(g, a, T, S, H, head, 32, t, s_tab, grec, cnt);
+    // move the (< 32) waiting entries to the front
+    const uint32_t left = nq - head;
+    uint32_t mi = 0, mp = 0;
+    if (lane < left) {
+        mi = H.idx[head + lane];
+        mp = H.pk[head + lane];
+    }
+    __syncwarp();
+    if (lane < left) {
+        H.idx[lane] = mi;
+        H.pk[lane] = mp;
+    }
+    nq = left;
+    __syncwarp();
 }
 
 // The calling warp checks the flat quad indices [f_begin, f_end) of the item
@@ -430,18 +466,19 @@ __device__ __forceinline__ void scan_flat(const GraphDev& g, const SurveyArgs& a
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
             const uint32_t rr[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+            int pos[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const uint32_t e = e0[u] + i;
-                const int pos = (e >= lo[u] && e < hi[u]) ? table_find(T, rr[i]) : -1;
-                push_hit<F>(pos, e, ks[u], nq, g, a, T, S, H, t, s_tab, grec, cnt);
+                pos[i] = (e >= lo[u] && e < hi[u]) ? table_find(T, rr[i]) : -1;
             }
+            push_quad<F>(pos, e0[u], ks[u], nq, g, a, T, S, H, t, s_tab, grec, cnt);
         }
         klo = khi - 1;
     }
     if (nq) {
         __syncwarp();
-        fold_queue<F>(g, a, T, S, H, nq, t, s_tab, grec, cnt);
+        fold_queue<F>(g, a, T, S, H, 0, nq, t, s_tab, grec, cnt);
     }
     __syncwarp();
 }
@@ -468,8 +505,10 @@ __device__ void flush_count(unsigned long long cnt, const SurveyArgs& a, unsigne
 // array of staged entries only for kinds that use degrees)
 template <int F, uint32_t CHUNK>
 constexpr size_t block_smem_fixed() {
-    return kWarps * kHitQ * 8 + 3 * CHUNK * 4 + CHUNK * 4 * ((F & F_EXTRA) ? 2 : 1) + 3 * CHUNK * 2 + CHUNK * 2 +
-           kBlockInEdges * 4 * 5 + (kBlockInEdges + 1) * 4;
+    return kWarps * kHitQ * 8 + kTableFactor * CHUNK * 4 + CHUNK * 4 * ((F & F_EXTRA) ? 2 : 1) +
+           kTableFactor * CHUNK * 2 +
+           CHUNK * (((F & F_EL) ? 1 : 0) + ((F & F_VL) ? 1 : 0)) + kBlockInEdges * 4 * ((F & F_EXTRA) ? 5 : 4) +
+           (kBlockInEdges + 1) * 4;
 }
 
 // CTR selects the item counter: 1 for the kBlockChunk list, 2 for the kBigChunk list.
@@ -477,7 +516,7 @@ template <int F, uint32_t CHUNK, int CTR>
 __global__ void __launch_bounds__(kBlockThreads, CHUNK <= kBlockChunk ? 5 : 3)
     survey_block_kernel(GraphDev g, const WorkItem* __restrict__ items,
                                                                      uint32_t n_items, SurveyArgs a) {
-    constexpr uint32_t kBlockTable = 3 * CHUNK;
+    constexpr uint32_t kBlockTable = kTableFactor * CHUNK;
     extern __shared__ __align__(16) unsigned char smem[];
     using BlockScan = cub::BlockScan<uint32_t, kBlockThreads>;
     __shared__ typename BlockScan::TempStorage scan_tmp;
@@ -494,15 +533,15 @@ __global__ void __launch_bounds__(kBlockThreads, CHUNK <= kBlockChunk ? 5 : 3)
     S.jend = S.j0 + kBlockInEdges;
     S.tpq = S.jend + kBlockInEdges;
     S.meta = S.tpq + kBlockInEdges;
-    S.p = S.meta + kBlockInEdges;
-    S.pp = S.p + kBlockInEdges;
+    S.p = S.meta + kBlockInEdges;  // present only with F_EXTRA
+    S.pp = S.p + ((F & F_EXTRA) ? kBlockInEdges : 0);
     uint32_t* hq = S.pp + kBlockInEdges + 1;
     HitQueue H;
     H.idx = hq + (threadIdx.x >> 5) * 2 * kHitQ;
     H.pk = H.idx + kHitQ;
     T.pos = reinterpret_cast<uint16_t*>(hq + kWarps * 2 * kHitQ);
-    T.el = reinterpret_cast<uint8_t*>(T.pos + kBlockTable);
-    T.vl = T.el + CHUNK;
+    T.el = reinterpret_cast<uint8_t*>(T.pos + kBlockTable);  // present only with F_EL
+    T.vl = T.el + ((F & F_EL) ? CHUNK : 0);                  // present only with F_VL
 
     for (uint32_t w = threadIdx.x; w < a.s_words; w += blockDim.x) s_tab[w] = 0;
     unsigned long long cnt = 0;
@@ -557,7 +596,7 @@ __global__ void __launch_bounds__(kBlockThreads, CHUNK <= kBlockChunk ? 5 : 3)
 
 // ---- warp kernel: one item per warp at a time ------------------------------------------------
 
-constexpr uint32_t kWTable = 3 * kWarpMaxQ;
+constexpr uint32_t kWTable = kTableFactor * kWarpMaxQ;
 struct __align__(16) WarpSmem {
     uint32_t key[kWTable];
     uint32_t ts[kWarpMaxQ];
