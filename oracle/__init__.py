@@ -45,9 +45,12 @@ def build(force: bool = False) -> str:
 
 
 def _load():
+    """The compiled oracle.  ``ORACLE_LIBRARY`` names another build of ``oracle.c`` to load
+    instead: the mutation tests point it at copies with a planted mistake."""
     global _lib
     if _lib is None:
-        lib = ctypes.CDLL(build())
+        path = os.environ.get("ORACLE_LIBRARY") or build()
+        lib = ctypes.CDLL(path)
         vp, u64, u32, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
         lib.oracle_survey.argtypes = [vp, vp, vp, vp, u64, vp, u32, u32, u32, u32, u32, i32, u32,
                                       u32, i32, ctypes.POINTER(_Out), ctypes.POINTER(_Stats)]

@@ -136,6 +136,16 @@ def test_complete_graph_closed_forms():
     assert r["degtri"][(5 * 33 + 5) * 33 + 5] == math.comb(n, 3)  # degree 29 -> ceil(log2 29) = 5
 
 
+def test_complete_graph_over_several_thread_blocks():
+    """K_600 with 4 threads: pivots fall in three blocks of 256, so every per-thread table is merged."""
+    n = 600
+    iu = np.triu_indices(n, 1)
+    r = run(iu[0], iu[1], np.arange(len(iu[0])), None, None, n, 1, 1, threads=4)
+    assert int(r["count"][0]) == math.comb(n, 3)
+    assert r["vlocal"].tolist() == [math.comb(n - 1, 2)] * n
+    assert int(r["degtri"][(10 * 33 + 10) * 33 + 10]) == math.comb(n, 3)  # degree 599 -> bin 10
+
+
 def test_bipartite_and_star_have_no_triangles():
     a, b = np.meshgrid(np.arange(10), np.arange(10, 25))
     r = run(a.ravel(), b.ravel(), np.zeros(a.size), None, None, 25, 1, 1)
@@ -223,16 +233,16 @@ def test_window_equals_filtered_subgraph():
 
 def test_pivot_ranges_and_threads_partition_the_survey():
     g = synth.rmat_graph(11, 16, 3, ts_bits=20, num_vlabels=4, num_elabels=2)
-    full = oracle.survey_graph(g, extras=("joint",))
+    full = oracle.survey_graph(g, extras=ALL_EXTRAS)
     cuts = [0, 100, 900, 1500, g.n]
-    acc = {k: np.zeros_like(full[k]) for k in ("count", "hist", "vtri", "etri", "joint")}
+    acc = {k: np.zeros_like(full[k]) for k in ("count", "hist", "vtri", "etri") + ALL_EXTRAS}
     for lo, hi in zip(cuts[:-1], cuts[1:]):
-        part = oracle.survey_graph(g, pivot_range=(lo, hi), extras=("joint",))
+        part = oracle.survey_graph(g, pivot_range=(lo, hi), extras=ALL_EXTRAS)
         for k in acc:
             acc[k] += part[k]
     for k in acc:
         assert np.array_equal(acc[k], full[k]), k
-    thr = oracle.survey_graph(g, threads=4, extras=("joint",))
+    thr = oracle.survey_graph(g, threads=4, extras=ALL_EXTRAS)
     for k in acc:
         assert np.array_equal(thr[k], full[k]), k
 
