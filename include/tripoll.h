@@ -142,7 +142,10 @@ uint64_t tripoll_result_words(uint32_t kind_mask, uint32_t num_vlabels, uint32_t
                               uint64_t num_vertices);
 
 /* Run one survey (Alg. 1 with the fold of the requested kinds) over every
- * triangle of g whose edge timestamps lie in [t_lo, t_hi].
+ * triangle of g whose edge timestamps lie in [t_lo, t_hi].  A window other
+ * than [0, 0xFFFFFFFF] first compacts G+ to its in-window edges (about
+ * 13 bytes per edge of stream-ordered pool memory, released when the survey
+ * ends), so that wedges through an out-of-window edge are never checked.
  *   result  device or host, uint64[tripoll_result_words(kinds, ...)]; overwritten.
  *           For a batched graph: uint64[num_graphs * words], graph i's tables
  *           at offset i * words.
@@ -168,7 +171,8 @@ int tripoll_survey_range(tripoll_graph_t g, uint32_t kind_mask, uint32_t t_lo, u
  * convenience.  Same arguments, kernels and result as tripoll_survey, but the
  * call allocates nothing: its scratch (the accumulation record and two work
  * counters) is a static 8 MiB device array that every GPU loading the library
- * holds until the process exits.
+ * holds until the process exits, and a window is applied in place (no window
+ * view: out-of-window edges are skipped where they are met).
  *   - The first call on a device looks up that array's device address; make
  *     the first call before any stream capture on that device.
  *   - Every call reuses the same array (each call clears the part it needs):
@@ -194,8 +198,10 @@ int tripoll_graph_stats(tripoll_graph_t g, tripoll_graph_info* info);
 
 /* Number of wedge checks (Sec. 3: a wedge (p,q),(p,r) with q <+ r, checked for
  * the closing edge (q,r)) that a survey over the window [t_lo, t_hi] performs:
- * the wedges whose edge (p,q) lies in the window (others cannot close into a
- * surveyed triangle).  [0, 0xFFFFFFFF] gives |W+|.  *out: host.  Synchronises. */
+ * the wedges of the subgraph of in-window edges, i.e. both (p,q) and (p,r) in
+ * the window (others cannot close into a surveyed triangle), sum over pivots p
+ * of C(k, 2) with k the in-window edges of Adj+(p).  [0, 0xFFFFFFFF] gives
+ * |W+|.  *out: host.  Synchronises. */
 int tripoll_wedge_checks(tripoll_graph_t g, uint32_t t_lo, uint32_t t_hi, uint64_t* out, void* cuda_stream);
 
 /* Copy out the built G+ (for checking the builder): any pointer may be NULL.
@@ -216,8 +222,10 @@ void tripoll_destroy(tripoll_graph_t g);
  * memory fit under scratch_cap_bytes and fewer than max_inflight requests are
  * on the device; admitted requests are launched together (one launch per
  * admission round, several rounds in flight on different streams), and every
- * request that arrives meanwhile joins the next round.  Results are the same
- * as tripoll_survey's for that request alone. */
+ * request that arrives meanwhile joins the next round.  A windowed request is
+ * charged its window view too (see tripoll_survey) when the budget holds both,
+ * and otherwise runs without one.  Results are the same as tripoll_survey's
+ * for that request alone. */
 int tripoll_server_create(uint64_t scratch_cap_bytes, uint32_t max_inflight,
                           tripoll_server_t* out);
 /* Make g resident in the server (the server does not take ownership). */

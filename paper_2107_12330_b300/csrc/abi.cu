@@ -104,13 +104,15 @@ __global__ void cut_kernel(const uint64_t* __restrict__ prefix, uint64_t n, uint
     bounds[i] = lo;
 }
 
-// wedge checks of a windowed survey: suffix lengths of the in-window in-edges
-__global__ void wedge_checks_kernel(const InEdge* __restrict__ in_edge, uint64_t m, uint32_t t_lo, uint32_t t_hi,
-                                    unsigned long long* out) {
+// wedges of the window's subgraph: sum over pivots p of C(k, 2), k the
+// number of in-window edges in Adj+(p)
+__global__ void wedge_checks_kernel(const uint64_t* __restrict__ off, const uint32_t* __restrict__ ts, uint64_t n,
+                                    uint32_t t_lo, uint32_t t_hi, unsigned long long* out) {
     unsigned long long w = 0;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
-        const InEdge ie = in_edge[i];
-        if (ie.ts >= t_lo && ie.ts <= t_hi) w += ie.end - ie.e - 1;
+    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < n; p += (uint64_t)gridDim.x * blockDim.x) {
+        unsigned long long k = 0;
+        for (uint64_t e = off[p]; e < off[p + 1]; ++e) k += (ts[e] >= t_lo && ts[e] <= t_hi) ? 1u : 0u;
+        w += k * (k ? k - 1 : 0) / 2;
     }
     for (int o = 16; o; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
     if ((threadIdx.x & 31) == 0 && w) atomicAdd(out, w);
@@ -128,8 +130,8 @@ extern "C" int tripoll_wedge_checks(tripoll_graph_t g, uint32_t t_lo, uint32_t t
     TP_CUDA(acc.alloc(8, s));
     TP_CUDA(cudaMemsetAsync(acc.ptr, 0, 8, s));
     if (g->m) {
-        wedge_checks_kernel<<<(unsigned)std::min<uint64_t>((g->m + 255) / 256, 148 * 32), 256, 0, s>>>(
-            g->in_edge, g->m, t_lo, t_hi, acc.as<unsigned long long>()); ::tp::note_launch();
+        wedge_checks_kernel<<<(unsigned)std::min<uint64_t>((g->n + 255) / 256, 148 * 32), 256, 0, s>>>(
+            g->off, g->ts, g->n, t_lo, t_hi, acc.as<unsigned long long>()); ::tp::note_launch();
         TP_CUDA(cudaGetLastError());
     }
     TP_CUDA(cudaMemcpyAsync(out, acc.ptr, 8, cudaMemcpyDeviceToHost, s));

@@ -88,6 +88,11 @@ struct GraphDev {
     const uint32_t* graph_of = nullptr; // [n] graph index by position (batched) or null
     const uint64_t* in_off = nullptr;   // [n+1]
     const InEdge* in_edge = nullptr;    // [m]
+    // Window view: when set, col/ts/el above hold only the edges whose timestamp
+    // lies in the survey's window (same order), and newpos[e] (e in [0, m]) is
+    // the number of such edges before CSR position e of G+; off, in_off and
+    // in_edge stay those of G+ and are translated through newpos.
+    const uint32_t* newpos = nullptr;   // [m+1] or null
 };
 
 }  // namespace tp
@@ -149,9 +154,14 @@ Layout make_layout(uint32_t kinds, uint32_t Lv, uint32_t Le, uint64_t n);
 
 int build_plan(tripoll_graph* g, cudaStream_t s);
 // Launch the survey kernels accumulating into `acc` (zeroed by the caller);
-// counters: device uint32[4] of scratch.
+// counters: device uint32[4] of scratch.  With window_view, a window that is
+// not [0, 0xFFFFFFFF] first compacts G+ to its in-window edges in pool memory
+// (window_view_bytes of it); without, out-of-window edges are skipped in place.
 int launch_survey(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_t t_hi, uint64_t p_lo,
-                  uint64_t p_hi, unsigned long long* acc, uint32_t* counters, cudaStream_t s);
+                  uint64_t p_hi, unsigned long long* acc, uint32_t* counters, cudaStream_t s,
+                  bool window_view = true);
+// Device scratch the window view of g takes for [t_lo, t_hi] (0 for the full window).
+uint64_t window_view_bytes(const tripoll_graph* g, uint32_t t_lo, uint32_t t_hi);
 int check_survey_args(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_t t_hi, const void* result);
 void free_graph_arrays(tripoll_graph* g);
 }  // namespace tp

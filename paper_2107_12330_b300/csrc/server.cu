@@ -35,6 +35,7 @@ struct Request {
     uint32_t slot = 0, kinds = 0, t_lo = 0, t_hi = 0;
     uint64_t words = 0;
     uint64_t bytes = 0;          // device scratch charged to the budget
+    bool view = false;           // survey through a window view of the graph
     uint64_t* host = nullptr;    // pinned result buffer
     size_t host_cap = 0;
     uint64_t t_submit = 0, t_done = 0;
@@ -83,10 +84,10 @@ void CUDART_CB on_request_done(void* arg) {
 int launch_request(tripoll_server* s, Request* r, cudaStream_t st) {
     tripoll_graph* g = s->graphs[r->slot];
     unsigned long long* acc = nullptr;
-    TP_CUDA(cudaMallocAsync((void**)&acc, r->bytes, st));
+    TP_CUDA(cudaMallocAsync((void**)&acc, r->words * 8 + 16, st));
     uint32_t* counters = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(acc) + r->words * 8);
     TP_CUDA(cudaMemsetAsync(acc, 0, r->words * 8, st));
-    int rc = launch_survey(g, r->kinds, r->t_lo, r->t_hi, 0, g->n, acc, counters, st);
+    int rc = launch_survey(g, r->kinds, r->t_lo, r->t_hi, 0, g->n, acc, counters, st, r->view);
     if (rc) {
         cudaFreeAsync(acc, st);
         return rc;
@@ -199,6 +200,10 @@ extern "C" int tripoll_server_submit(tripoll_server_t s, uint32_t slot, uint32_t
         delete r;
         return fail(TRIPOLL_ERR_NO_MEMORY, "request needs more scratch than the server budget");
     }
+    // the window view when the budget holds it too, else out-of-window edges are skipped in place
+    const uint64_t vb = window_view_bytes(g, t_lo, t_hi);
+    r->view = vb > 0 && r->bytes + vb <= s->cap;
+    if (r->view) r->bytes += vb;
     {  // pinned result buffer from the pool
         std::lock_guard<std::mutex> lk(s->mu);
         auto it = s->pinned_pool.lower_bound(r->words * 8);

@@ -67,7 +67,7 @@ extern "C" int tripoll_survey_static(tripoll_graph_t g, uint32_t kind_mask, uint
     uint32_t* counters = reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(base) + record_bytes);
     // the array keeps the previous call's contents: clear the record first
     TP_CUDA(cudaMemsetAsync(acc, 0, words * 8, s));
-    if (g->n && (rc = launch_survey(g, kind_mask, t_lo, t_hi, 0, g->n, acc, counters, s))) return rc;
+    if (g->n && (rc = launch_survey(g, kind_mask, t_lo, t_hi, 0, g->n, acc, counters, s, false))) return rc;
     TP_CUDA(cudaMemcpyAsync(result, acc, words * 8, cudaMemcpyDefault, s));
     if (!is_device_pointer(result)) TP_CUDA(cudaStreamSynchronize(s));
     return TRIPOLL_OK;

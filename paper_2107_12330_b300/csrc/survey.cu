@@ -30,6 +30,8 @@
 // then with 64-bit global atomics once per block -- integer adds commute, so
 // the result is exact and schedule-independent.
 #include <cub/cub.cuh>
+#include <thrust/iterator/counting_iterator.h>
+#include <thrust/iterator/transform_iterator.h>
 
 #include <algorithm>
 #include <map>
@@ -201,6 +203,14 @@ constexpr uint32_t kTableFactor = TP_TABLE_FACTOR;  // table slots per staged en
 
 __device__ __forceinline__ uint32_t table_size(uint32_t len) { return max(kTableFactor * len, 4u); }
 
+// Slots used for len staged entries out of cap: a window view stages only
+// in-window entries, so its tables may use twice the slots per entry (load
+// factor <= 1/6 while they fit), like the in-place path whose out-of-window
+// entries are left out of a table sized for all of them.
+__device__ __forceinline__ uint32_t view_table_size(uint32_t len, bool view, uint32_t cap) {
+    return view ? min(table_size(2 * len), cap) : table_size(len);
+}
+
 // Insert the entries [i0, len) step `stride` of the staged out-list part at
 // CSR position qbase; entries whose (q,r) timestamp lies outside the window
 // can close no surveyed triangle and are left out.
@@ -294,6 +304,10 @@ __device__ __forceinline__ uint32_t stage_in_edge(const GraphDev& g, const Surve
         p = lo;
     }
     uint32_t j0 = ie.e + 1, jend = ie.end;
+    if (ok && g.newpos) {  // the suffix of Adj+(p) after q in the window view
+        j0 = __ldg(&g.newpos[ie.e]) + 1;
+        jend = __ldg(&g.newpos[ie.end]);
+    }
     if (ok && chunked && j0 < jend) {
         j0 = lower_bound_col(g.col, j0, jend, vlo);
         jend = upper_bound_col(g.col, j0, jend, vhi);
@@ -560,9 +574,18 @@ __global__ void __launch_bounds__(kBlockThreads, CHUNK <= kBlockChunk ? 5 : 3)
             cnt = 0;
         }
         grec_prev = grec;
-        const uint32_t qbase = (uint32_t)g.off[q] + item.qlo;
-        const uint32_t len = item.qlen;
-        T.size = table_size(len);
+        uint32_t qbase = (uint32_t)g.off[q] + item.qlo;
+        uint32_t len = item.qlen;
+        if (g.newpos) {  // the item's part of Adj+(q) in the window view
+            const uint32_t b0 = __ldg(&g.newpos[qbase]);
+            len = __ldg(&g.newpos[qbase + len]) - b0;
+            qbase = b0;
+            if (len == 0) {  // no in-window (q,r): no triangle; s_item is read by all before it changes
+                __syncthreads();
+                continue;
+            }
+        }
+        T.size = view_table_size(len, g.newpos != nullptr, kBlockTable);
         const uint32_t tsize = T.size;
         for (uint32_t i = threadIdx.x; i < tsize; i += blockDim.x) T.key[i] = kEmpty;
         __syncthreads();
@@ -639,9 +662,15 @@ __global__ void __launch_bounds__(kBlockThreads) survey_warp_kernel(GraphDev g, 
             cnt = 0;
         }
         grec_prev = grec;
-        const uint32_t qbase = (uint32_t)g.off[q];
-        const uint32_t len = item.qlen;
-        T.size = table_size(len);
+        uint32_t qbase = (uint32_t)g.off[q];
+        uint32_t len = item.qlen;
+        if (g.newpos) {  // Adj+(q) in the window view
+            const uint32_t b0 = __ldg(&g.newpos[qbase]);
+            len = __ldg(&g.newpos[qbase + len]) - b0;
+            qbase = b0;
+            if (len == 0) continue;  // no in-window (q,r): no triangle
+        }
+        T.size = view_table_size(len, g.newpos != nullptr, kWTable);
         const uint32_t tsize = T.size;
         __syncwarp();
         for (uint32_t i = lane; i < tsize; i += 32) ws.key[i] = kEmpty;
@@ -771,8 +800,7 @@ int blocks_per_sm(const void* kernel, size_t smem) {
 }
 
 template <int F>
-void launch_f(const tripoll_graph* g, const SurveyArgs& a, cudaStream_t s, int sms) {
-    GraphDev gd = g->dev();
+void launch_f(const tripoll_graph* g, const GraphDev& gd, const SurveyArgs& a, cudaStream_t s, int sms) {
     if (g->n_items_warp) {
         size_t sm = ((a.s_words * 8 + 15) & ~15u) + kWarps * sizeof(WarpSmem);
         const int per = blocks_per_sm((const void*)survey_warp_kernel<F>, sm);
@@ -797,7 +825,48 @@ void launch_f(const tripoll_graph* g, const SurveyArgs& a, cudaStream_t s, int s
     }
 }
 
-using LaunchFn = void (*)(const tripoll_graph*, const SurveyArgs&, cudaStream_t, int);
+using LaunchFn = void (*)(const tripoll_graph*, const GraphDev&, const SurveyArgs&, cudaStream_t, int);
+
+// ---- window view: G+ restricted to the edges in the window ----------------------------------
+//
+// A triangle is surveyed iff its three edges lie in the window, so the survey
+// over [t_lo, t_hi] is the survey of the subgraph of in-window edges under the
+// same order <+.  Compacting col/ts/el to that subgraph before the wedge
+// checks removes the wedges (p,q),(p,r) whose (p,r) lies outside the window:
+// with a window holding a fraction f of the edges, the checks drop from about
+// f |W+| (in-place skipping of (p,q) and (q,r) only) to about f^2 |W+|.
+
+// 1 for CSR positions e < m whose timestamp lies in the window, 0 for e = m.
+struct InWindow {
+    const uint32_t* ts;
+    uint64_t m;
+    uint32_t lo, hi;
+    __host__ __device__ uint32_t operator()(uint64_t e) const {
+        return (e < m && ts[e] >= lo && ts[e] <= hi) ? 1u : 0u;
+    }
+};
+
+__global__ void window_view_kernel(const uint32_t* __restrict__ col, const uint32_t* __restrict__ ts,
+                                   const uint8_t* __restrict__ el, const uint32_t* __restrict__ newpos, uint64_t m,
+                                   uint32_t lo, uint32_t hi, uint32_t* __restrict__ vcol, uint32_t* __restrict__ vts,
+                                   uint8_t* __restrict__ vel) {
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < m; e += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t t = ts[e];
+        if (t < lo || t > hi) continue;
+        const uint32_t p = newpos[e];
+        vcol[p] = col[e];
+        vts[p] = t;
+        if (el) vel[p] = el[e];
+    }
+}
+
+size_t window_scan_bytes(uint64_t m) {
+    auto flags = thrust::make_transform_iterator(thrust::counting_iterator<uint64_t>(0),
+                                                 InWindow{nullptr, m, 0u, 0u});
+    size_t tb = 0;
+    cub::DeviceScan::ExclusiveSum(nullptr, tb, flags, (uint32_t*)nullptr, m + 1);
+    return tb;
+}
 constexpr LaunchFn kLaunch[16] = {&launch_f<0>,  &launch_f<1>,  &launch_f<2>,  &launch_f<3>,
                                   &launch_f<4>,  &launch_f<5>,  &launch_f<6>,  &launch_f<7>,
                                   &launch_f<8>,  &launch_f<9>,  &launch_f<10>, &launch_f<11>,
@@ -840,9 +909,17 @@ int build_plan(tripoll_graph* g, cudaStream_t s) {
     return TRIPOLL_OK;
 }
 
+uint64_t window_view_bytes(const tripoll_graph* g, uint32_t t_lo, uint32_t t_hi) {
+    if ((t_lo == 0 && t_hi == 0xFFFFFFFFu) || !g->m) return 0;
+    const uint64_t m = g->m;
+    const uint64_t r = 256;  // pool rounding per allocation
+    return (m + 1) * 4 + r + 2 * ((m + kColPad) * 4 + r) + (g->el ? m + kColPad + r : 0) +
+           window_scan_bytes(m) + r;
+}
+
 // Launch the survey kernels accumulating into `acc` (zeroed by the caller).
 int launch_survey(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_t t_hi, uint64_t p_lo, uint64_t p_hi,
-                  unsigned long long* acc, uint32_t* counters, cudaStream_t s) {
+                  unsigned long long* acc, uint32_t* counters, cudaStream_t s, bool window_view) {
     const Layout lay = make_layout(kinds, g->Lv, g->Le, g->n);
     SurveyArgs a;
     a.kinds = kinds;
@@ -880,7 +957,29 @@ int launch_survey(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
     TP_CUDA(cudaMemsetAsync(counters, 0, 16, s));
-    kLaunch[F](g, a, s, sms);
+    GraphDev gd = g->dev();
+    Scratch vpos, vcol, vts, vel, vtmp;  // released (stream-ordered) after the survey kernels
+    if (window && window_view && g->m) {
+        const uint64_t m = g->m;
+        TP_CUDA(vpos.alloc((m + 1) * 4, s));
+        TP_CUDA(vcol.alloc((m + kColPad) * 4, s));
+        TP_CUDA(vts.alloc((m + kColPad) * 4, s));
+        if (g->el) TP_CUDA(vel.alloc(m + kColPad, s));
+        auto flags = thrust::make_transform_iterator(thrust::counting_iterator<uint64_t>(0),
+                                                     InWindow{g->ts, m, t_lo, t_hi});
+        size_t tb = window_scan_bytes(m);
+        TP_CUDA(vtmp.alloc(tb, s));
+        TP_CUDA(cub::DeviceScan::ExclusiveSum(vtmp.ptr, tb, flags, vpos.as<uint32_t>(), m + 1, s));
+        window_view_kernel<<<grid_n(m), 256, 0, s>>>(g->col, g->ts, g->el, vpos.as<uint32_t>(), m, t_lo, t_hi,
+                                                     vcol.as<uint32_t>(), vts.as<uint32_t>(),
+                                                     g->el ? vel.as<uint8_t>() : nullptr); ::tp::note_launch();
+        TP_CUDA(cudaGetLastError());
+        gd.col = vcol.as<uint32_t>();
+        gd.ts = vts.as<uint32_t>();
+        gd.el = g->el ? vel.as<uint8_t>() : nullptr;
+        gd.newpos = vpos.as<uint32_t>();
+    }
+    kLaunch[F](g, gd, a, s, sms);
     TP_CUDA(cudaGetLastError());
     return TRIPOLL_OK;
 }

@@ -83,6 +83,45 @@ def test_complete_graph_long_out_lists():
     g = synth.Graph("K1100", n, src, dst, ts, vl, el, 3, 3, BASIC)
     got = check(g, BASIC)
     assert int(got[0]) == n * (n - 1) * (n - 2) // 6
+    # a window: the chunks' value ranges come from their in-window entries only
+    check(g, ALL & ~tp.TRIPOLL_VERTEX_LOCAL, window=(1 << 14, 3 << 14))
+    check(g, tp.TRIPOLL_COUNT | tp.TRIPOLL_VERTEX_LOCAL, window=(0, 1 << 12))
+
+
+def _numpy_window_wedges(g, lo, hi):
+    """Sum over pivots p of C(k_p, 2), k_p the in-window edges of Adj+(p): dedup keeping the
+    first record, (degree, id) order, orientation low -> high, all in numpy."""
+    u = np.minimum(g.src, g.dst).astype(np.int64)
+    v = np.maximum(g.src, g.dst).astype(np.int64)
+    el = g.elabel if g.elabel is not None else np.zeros(len(u), np.uint8)
+    keep = u != v
+    u, v, t, e = u[keep], v[keep], g.ts[keep].astype(np.int64), el[keep]
+    o = np.lexsort((e, t, v, u))
+    u, v, t = u[o], v[o], t[o]
+    first = np.ones(len(u), bool)
+    first[1:] = (u[1:] != u[:-1]) | (v[1:] != v[:-1])
+    u, v, t = u[first], v[first], t[first]
+    deg = np.bincount(u, minlength=g.n) + np.bincount(v, minlength=g.n)
+    rank = np.empty(g.n, np.int64)
+    rank[np.lexsort((np.arange(g.n), deg))] = np.arange(g.n)
+    piv = np.where(rank[u] < rank[v], u, v)
+    inw = (t >= lo) & (t <= hi)
+    k = np.bincount(piv[inw], minlength=g.n).astype(np.int64)
+    return int((k * (k - 1) // 2).sum()), int(len(u))
+
+
+def test_wedge_checks_of_a_window():
+    g = synth.rmat(13, 3)
+    h = build(g)
+    try:
+        st = tp.tripoll_graph_stats(h)
+        assert tp.tripoll_wedge_checks(h) == st["wedges"]
+        for lo, hi in [g.window, (0, 0), (1 << 29, 0xFFFFFFFF)]:
+            want, m = _numpy_window_wedges(g, lo, hi)
+            assert m == st["num_edges"]
+            assert tp.tripoll_wedge_checks(h, lo, hi) == want
+    finally:
+        tp.tripoll_destroy(h)
 
 
 def test_rmat16_window_edge_label_triples():
