@@ -237,25 +237,38 @@ __device__ __forceinline__ void table_fill(const GraphDev& g, const SurveyArgs& 
     }
 }
 
-// Index of r among the staged entries, or -1.
+// Index of r among the staged entries, or -1, searching from slot h on.
 template <class PosT>
-__device__ __forceinline__ int table_find(const QTable<PosT>& T, uint32_t r) {
-    uint32_t h = hash_slot(r, T.size);
-#ifdef TP_PROBE2
-    // the home slot and the next one are read together; most searches end there
-    uint32_t h1 = h + 1 == T.size ? 0u : h + 1;
-    const uint32_t k0 = T.key[h], k1 = T.key[h1];
-    if (k0 == r) return (int)T.pos[h];
-    if (k0 == kEmpty) return -1;
-    if (k1 == r) return (int)T.pos[h1];
-    if (k1 == kEmpty) return -1;
-    h = h1 + 1 == T.size ? 0u : h1 + 1;
-#endif
+__device__ __forceinline__ int table_find_from(const QTable<PosT>& T, uint32_t r, uint32_t h) {
     while (true) {
         const uint32_t key = T.key[h];
         if (key == r) return (int)T.pos[h];
         if (key == kEmpty) return -1;
         if (++h == T.size) h = 0;
+    }
+}
+
+// The four candidates of a quad (act[i]: position i lies in the segment): the
+// four home slots are read together, and only a home slot holding another
+// key continues the search.
+template <class PosT>
+__device__ __forceinline__ void probe_quad(const QTable<PosT>& T, const uint32_t (&r)[4], const bool (&act)[4],
+                                           int (&pos)[4]) {
+    uint32_t h[4], key[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        h[i] = hash_slot(r[i], T.size);
+        key[i] = act[i] ? T.key[h[i]] : kEmpty;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        pos[i] = -1;
+        if (key[i] == kEmpty) continue;
+        if (key[i] == r[i]) {
+            pos[i] = (int)T.pos[h[i]];
+            continue;
+        }
+        pos[i] = table_find_from(T, r[i], h[i] + 1 == T.size ? 0u : h[i] + 1);
     }
 }
 
@@ -333,7 +346,7 @@ __device__ __forceinline__ uint32_t seg_of(const uint32_t* pp, uint32_t lo, uint
 #define TP_UNROLL 2
 #endif
 constexpr int kUnroll = TP_UNROLL;  // quads each lane has in flight per chunk
-constexpr int kHitQ = 160;  // per-warp queue of hits awaiting the fold (< 32 left + 4 x 32 new)
+constexpr int kHitQ = 64;  // per-warp queue of hits awaiting the fold (< 32 left + 32 new)
 
 // Per-warp queue of wedge checks that hit: CSR position of (p,r), and
 // (staged index of r) | (in-edge slot) << 16.
@@ -376,9 +389,9 @@ __device__ __forceinline__ void fold_queue(const GraphDev& g, const SurveyArgs& 
 }
 
 // Queue the hits of this lane's quad -- pos[i] >= 0 for a hit at CSR position
-// e0 + i of in-edge slot k -- with one ballot per quad position, and fold the
-// queue 32 entries at a time while 32 or more are waiting.  Called by the
-// whole warp; nq (< 32 on entry and exit) is warp-uniform.
+// e0 + i of in-edge slot k -- one ballot per quad position, and fold 32 queued
+// hits, all lanes active, whenever 32 are waiting.  Called by the whole warp;
+// nq (< 32 on entry and exit) is warp-uniform.
 template <int F, class PosT>
 __device__ __forceinline__ void push_quad(const int (&pos)[4], uint32_t e0, uint32_t k, uint32_t& nq,
                                           const GraphDev& g, const SurveyArgs& a, const QTable<PosT>& T,
@@ -387,39 +400,35 @@ __device__ __forceinline__ void push_quad(const int (&pos)[4], uint32_t e0, uint
                                           unsigned long long& cnt) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
-    unsigned b[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) b[i] = __ballot_sync(0xffffffffu, pos[i] >= 0);
-    if (!(b[0] | b[1] | b[2] | b[3])) return;
-    uint32_t off = nq;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
+        const unsigned b = __ballot_sync(0xffffffffu, pos[i] >= 0);
+        if (!b) continue;
         if (pos[i] >= 0) {
-            const uint32_t slot = off + __popc(b[i] & lt);
+            const uint32_t slot = nq + __popc(b & lt);
             H.idx[slot] = e0 + i;
             H.pk[slot] = (uint32_t)pos[i] | (k << 16);
         }
-        off += __popc(b[i]);
+        nq += __popc(b);
+        if (nq >= 32) {
+            __syncwarp();
+            fold_queue<F>(g, a, T, S, H, 0, 32, t, s_tab, grec, cnt);
+            // move the (< 32) waiting entries to the front
+            const uint32_t left = nq - 32;
+            uint32_t mi = 0, mp = 0;
+            if (lane < left) {
+                mi = H.idx[32 + lane];
+                mp = H.pk[32 + lane];
+            }
+            __syncwarp();
+            if (lane < left) {
+                H.idx[lane] = mi;
+                H.pk[lane] = mp;
+            }
+            nq = left;
+            __syncwarp();
+        }
     }
-    nq = off;
-    if (nq < 32) return;
-    __syncwarp();
-    uint32_t head = 0;
-    for (; nq - head >= 32; head += 32) fold_queue<F>(g, a, T, S, H, head, 32, t, s_tab, grec, cnt);
-    // move the (< 32) waiting entries to the front
-    const uint32_t left = nq - head;
-    uint32_t mi = 0, mp = 0;
-    if (lane < left) {
-        mi = H.idx[head + lane];
-        mp = H.pk[head + lane];
-    }
-    __syncwarp();
-    if (lane < left) {
-        H.idx[lane] = mi;
-        H.pk[lane] = mp;
-    }
-    nq = left;
-    __syncwarp();
 }
 
 // The calling warp checks the flat quad indices [f_begin, f_end) of the item
@@ -480,12 +489,11 @@ __device__ __forceinline__ void scan_flat(const GraphDev& g, const SurveyArgs& a
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
             const uint32_t rr[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
-            int pos[4];
+            bool act[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const uint32_t e = e0[u] + i;
-                pos[i] = (e >= lo[u] && e < hi[u]) ? table_find(T, rr[i]) : -1;
-            }
+            for (int i = 0; i < 4; ++i) act[i] = e0[u] + i >= lo[u] && e0[u] + i < hi[u];
+            int pos[4];
+            probe_quad(T, rr, act, pos);
             push_quad<F>(pos, e0[u], ks[u], nq, g, a, T, S, H, t, s_tab, grec, cnt);
         }
         klo = khi - 1;
