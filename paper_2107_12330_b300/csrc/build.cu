@@ -162,7 +162,7 @@ __global__ void rank_kernel(const uint64_t* __restrict__ vkey, uint64_t n, int b
 }
 
 __global__ void orient_kernel(const uint64_t* __restrict__ ukey, uint64_t m, int b, const uint32_t* __restrict__ rank,
-                              uint64_t* __restrict__ okey, uint32_t* __restrict__ dplus) {
+                              uint64_t* __restrict__ okey) {
     const uint64_t mask = (1ull << b) - 1;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m;
          i += (uint64_t)gridDim.x * blockDim.x) {
@@ -170,8 +170,26 @@ __global__ void orient_kernel(const uint64_t* __restrict__ ukey, uint64_t m, int
         uint64_t ru = rank[k >> b], rv = rank[k & mask];
         uint64_t s = ru < rv ? ru : rv, d = ru < rv ? rv : ru;
         okey[i] = (s << b) | d;
-        atomicAdd(&dplus[s], 1u);
     }
+}
+
+// Runs of equal (key >> shift) in keys sorted ascending: first[v] and last[v]
+// get the run of value v as [first, last) (both left 0 for absent values), so
+// that last - first counts the keys of v without atomics.
+template <class K>
+__global__ void run_ends_kernel(const K* __restrict__ key, uint64_t m, int shift, uint32_t* __restrict__ first,
+                                uint32_t* __restrict__ last) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t v = (uint64_t)(key[i] >> shift);
+        if (i == 0 || (uint64_t)(key[i - 1] >> shift) != v) first[v] = (uint32_t)i;
+        if (i + 1 == m || (uint64_t)(key[i + 1] >> shift) != v) last[v] = (uint32_t)(i + 1);
+    }
+}
+
+__global__ void run_count_kernel(const uint32_t* __restrict__ first, uint32_t* __restrict__ last_cnt, uint64_t n) {
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x)
+        last_cnt[v] -= first[v];
 }
 
 // CSR arrays of G+ from the (source, target)-sorted edges, plus, in the same
@@ -180,7 +198,7 @@ __global__ void orient_kernel(const uint64_t* __restrict__ ukey, uint64_t m, int
 __global__ void csr_fill_kernel(const uint64_t* __restrict__ okey, const uint64_t* __restrict__ oval, uint64_t m,
                                 int b, const uint64_t* __restrict__ off, const uint8_t* __restrict__ vl,
                                 uint32_t* __restrict__ col, uint32_t* __restrict__ ts, uint8_t* __restrict__ el,
-                                InEdge* __restrict__ rec, uint32_t* __restrict__ ckey, uint32_t* __restrict__ din) {
+                                InEdge* __restrict__ rec, uint32_t* __restrict__ ckey) {
     const uint64_t mask = (1ull << b) - 1;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m;
          i += (uint64_t)gridDim.x * blockDim.x) {
@@ -197,7 +215,6 @@ __global__ void csr_fill_kernel(const uint64_t* __restrict__ okey, const uint64_
         ie.meta = l | ((uint32_t)vl[s] << 8);
         rec[i] = ie;
         ckey[i] = d;
-        atomicAdd(&din[d], 1u);
     }
 }
 
@@ -233,6 +250,22 @@ __global__ void stats_kernel(const uint64_t* __restrict__ off, const uint64_t* _
         if (dm) atomicMax(&stats[2], dm);
         if (gm) atomicMax(&stats[3], gm);
     }
+}
+
+// off[0..n] = exclusive prefix of the run lengths of (key >> shift) over m
+// keys sorted ascending (first, cnt: scratch of n + 1 words; tmp: scan scratch).
+template <class K>
+cudaError_t out_offsets(const K* key, uint64_t m, int shift, uint64_t n, uint32_t* first, uint32_t* cnt, uint64_t* off,
+                        void* tmp, size_t tb, cudaStream_t s) {
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(first, 0, (n + 1) * 4, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(cnt, 0, (n + 1) * 4, s)) != cudaSuccess) return e;
+    if (m) {
+        run_ends_kernel<K><<<grid_for(m), kThreads, 0, s>>>(key, m, shift, first, cnt); ::tp::note_launch();
+        if (n) { run_count_kernel<<<grid_for(n), kThreads, 0, s>>>(first, cnt, n); ::tp::note_launch(); }
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cub::DeviceScan::ExclusiveSum(tmp, tb, cnt, off, n + 1, s);
 }
 
 // Device copy of a caller array that may live in host memory.
@@ -475,44 +508,41 @@ int build_impl(const uint32_t* src_h, const uint32_t* dst_h, const uint32_t* ts_
     TP_CUDA(dalloc(&g->in_off, n + 1, s));
     TP_CUDA(dalloc(&g->in_edge, m, s));
     {
-        Scratch ok0, ok1, ov1, cnt, tmp;
+        Scratch ok0, ok1, ov1, first, cnt, tmp;
         TP_CUDA(ok0.alloc(m * 8, s));
         TP_CUDA(ok1.alloc(m * 8, s));
         TP_CUDA(ov1.alloc(m * 8, s));
+        TP_CUDA(first.alloc((n + 1) * 4, s));
         TP_CUDA(cnt.alloc((n + 1) * 4, s));
-        TP_CUDA(cudaMemsetAsync(cnt.ptr, 0, (n + 1) * 4, s));
         if (m)
             orient_kernel<<<grid_for(m), kThreads, 0, s>>>(ukey_d.as<uint64_t>(), m, b, rank_d.as<uint32_t>(),
-                                                           ok0.as<uint64_t>(), cnt.as<uint32_t>()); ::tp::note_launch();
+                                                           ok0.as<uint64_t>()); ::tp::note_launch();
         TP_CUDA(cudaGetLastError());
         ukey_d.release();
         rank_d.release();
-        // offsets: exclusive scan of out-degrees (m < 2^32, so 32-bit sums are exact)
-        size_t tb = 0;
-        TP_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tb, cnt.as<uint32_t>(), g->off, n + 1, s));
-        TP_CUDA(tmp.alloc(tb, s));
-        TP_CUDA(cub::DeviceScan::ExclusiveSum(tmp.ptr, tb, cnt.as<uint32_t>(), g->off, n + 1, s));
         cub::DoubleBuffer<uint64_t> kb(ok0.as<uint64_t>(), ok1.as<uint64_t>());
         cub::DoubleBuffer<uint64_t> vb(uval_d.as<uint64_t>(), ov1.as<uint64_t>());
-        size_t tb2 = 0;
+        size_t tb = 0, tb2 = 0;
+        TP_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tb, cnt.as<uint32_t>(), g->off, n + 1, s));
         const int end_bit = std::min(64, 2 * b);
         TP_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tb2, kb, vb, m, 0, end_bit, s));
-        if (tb2 > tb) TP_CUDA(tmp.alloc(tb2, s));
+        TP_CUDA(tmp.alloc(std::max(tb, tb2), s));
+        tb = tb2 = std::max(tb, tb2);
         TP_CUDA(cub::DeviceRadixSort::SortPairs(tmp.ptr, tb2, kb, vb, m, 0, end_bit, s));
+        // offsets: out-list lengths from the runs of equal sources, exclusive scan
+        // (m < 2^32, so 32-bit sums are exact)
+        TP_CUDA(out_offsets(kb.Current(), m, b, n, first.as<uint32_t>(), cnt.as<uint32_t>(), g->off, tmp.ptr, tb, s));
         // CSR arrays and in-edge records in CSR order; a stable sort by target then
         // leaves the records in (target, source) order
         Scratch ck0, ck1, rec1;
         TP_CUDA(ck0.alloc(m * 4, s));
         TP_CUDA(ck1.alloc(m * 4, s));
         TP_CUDA(rec1.alloc(m * sizeof(InEdge), s));
-        TP_CUDA(cudaMemsetAsync(cnt.ptr, 0, (n + 1) * 4, s));
         if (m)
             csr_fill_kernel<<<grid_for(m), kThreads, 0, s>>>(kb.Current(), vb.Current(), m, b, g->off, g->vl, g->col,
-                                                             g->ts, g->el, g->in_edge, ck0.as<uint32_t>(),
-                                                             cnt.as<uint32_t>()); ::tp::note_launch();
+                                                             g->ts, g->el, g->in_edge, ck0.as<uint32_t>()); ::tp::note_launch();
         TP_CUDA(cudaGetLastError());
         ok0.release(); ok1.release(); ov1.release(); uval_d.release();
-        TP_CUDA(cub::DeviceScan::ExclusiveSum(tmp.ptr, tb, cnt.as<uint32_t>(), g->in_off, n + 1, s));
         cub::DoubleBuffer<uint32_t> ckb(ck0.as<uint32_t>(), ck1.as<uint32_t>());
         cub::DoubleBuffer<InEdge> reb(g->in_edge, rec1.as<InEdge>());
         size_t tb3 = 0;
@@ -523,6 +553,9 @@ int build_impl(const uint32_t* src_h, const uint32_t* dst_h, const uint32_t* ts_
         TP_CUDA(cub::DeviceRadixSort::SortPairs(tmp3.ptr, tb3, ckb, reb, m, 0, tbits, s));
         if (m && reb.Current() != g->in_edge)
             TP_CUDA(cudaMemcpyAsync(g->in_edge, reb.Current(), m * sizeof(InEdge), cudaMemcpyDeviceToDevice, s));
+        // in-edge offsets from the runs of equal targets
+        TP_CUDA(out_offsets(ckb.Current(), m, 0, n, first.as<uint32_t>(), cnt.as<uint32_t>(), g->in_off, tmp.ptr, tb,
+                            s));
     }
     (void)vmask;
 
