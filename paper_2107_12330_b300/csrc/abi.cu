@@ -39,6 +39,15 @@ bool is_device_pointer(const void* p) {
     return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
 }
 
+bool is_pinned_host_pointer(const void* p) {
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return attr.type == cudaMemoryTypeHost;
+}
+
 int check_survey_args(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_t t_hi, const void* result) {
     if (!g) return fail(TRIPOLL_ERR_INVALID_ARG, "graph handle is NULL");
     if (!result) return fail(TRIPOLL_ERR_INVALID_ARG, "result is NULL");

@@ -271,7 +271,8 @@ cudaError_t out_offsets(const K* key, uint64_t m, int shift, uint64_t n, uint32_
 // Device copy of a caller array that may live in host memory.
 // Large pageable host arrays are page-locked in place for the copy (a DMA
 // straight from the caller's pages instead of the driver's bounce buffers) and
-// released once the stream has consumed them.
+// released once the stream has consumed them; page-locked arrays are copied as
+// they are.
 struct Input {
     const void* dptr = nullptr;
     Scratch copy;
@@ -281,7 +282,7 @@ struct Input {
         if (!p) { dptr = nullptr; return TRIPOLL_OK; }
         if (is_device_pointer(p)) { dptr = p; return TRIPOLL_OK; }
         TP_CUDA(copy.alloc(bytes, s));
-        if (bytes >= (size_t(64) << 20)) {
+        if (bytes >= (size_t(64) << 20) && !is_pinned_host_pointer(p)) {
             if (cudaHostRegister(const_cast<void*>(p), bytes, cudaHostRegisterReadOnly) == cudaSuccess) {
                 pinned = p;
                 stream = s;

@@ -50,6 +50,8 @@ void note_launch();
 
 // Is p device-accessible memory (device or managed allocation)?
 bool is_device_pointer(const void* p);
+// Is p page-locked host memory (cudaHostAlloc or registered)?
+bool is_pinned_host_pointer(const void* p);
 
 // ---- the built graph G+ ------------------------------------------------------------------------
 
