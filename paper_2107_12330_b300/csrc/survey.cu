@@ -18,10 +18,9 @@
 // tables of kBigChunk entries for longer ones (longer still are cut into
 // chunks and each in-edge's segment is restricted to the chunk's value range
 // by binary search).  Inside an item the in-edges' segments form one flat index space of
-// wedge checks that warps split evenly and walk in chunks of 32 x kUnroll: consecutive lanes
-// read consecutive suffix entries (coalesced), every lane keeps kUnroll
-// independent loads in flight, and no lane idles however skewed the suffix
-// lengths are.  Triangles outside the time window are pruned before any
+// units of 8 consecutive candidates that warps split evenly and walk 32 units at a
+// time: consecutive lanes read consecutive 32-byte units of the suffixes
+// (coalesced), and no lane idles however skewed the suffix lengths are.  Triangles outside the time window are pruned before any
 // probe where possible: in-edges (p,q) outside the window get empty segments
 // and entries (q,r) outside it are not inserted.
 //
@@ -204,11 +203,11 @@ constexpr uint32_t kTableFactor = TP_TABLE_FACTOR;  // table slots per staged en
 __device__ __forceinline__ uint32_t table_size(uint32_t len) { return max(kTableFactor * len, 4u); }
 
 // Slots used for len staged entries out of cap: a window view stages only
-// in-window entries, so its tables may use twice the slots per entry (load
-// factor <= 1/6 while they fit), like the in-place path whose out-of-window
-// entries are left out of a table sized for all of them.
+// in-window entries, so its tables use the room left by the out-of-window
+// ones: four times the slots per entry (load factor <= 1/12) while they fit,
+// which makes a probe that finds its home slot taken by another key rare.
 __device__ __forceinline__ uint32_t view_table_size(uint32_t len, bool view, uint32_t cap) {
-    return view ? min(table_size(2 * len), cap) : table_size(len);
+    return view ? min(table_size(4 * len), cap) : table_size(len);
 }
 
 // Insert the entries [i0, len) step `stride` of the staged out-list part at
@@ -277,9 +276,17 @@ __device__ __forceinline__ void probe_quad(const QTable<PosT>& T, const uint32_t
 // Per in-edge (p,q) of the item: the segment [j0, jend) of Adj+(p) to check
 // (positions after q, restricted to the staged value range of a chunked
 // item), the (p,q) metadata, and the exclusive prefix pp of the segments'
-// quad counts, a quad being 4 consecutive positions starting at a multiple of
-// 4: the item's wedge checks form one flat index space of quads
-// [0, pp[n_in]), each quad read with one 16-byte load.
+// unit counts, a unit being kUnit consecutive positions starting at a multiple
+// of kUnit: the item's wedge checks form one flat index space of units
+// [0, pp[n_in]), each unit read with kUnit/4 16-byte loads.
+#ifndef TP_UNIT_LOG
+#define TP_UNIT_LOG 3
+#endif
+constexpr uint32_t kUnitLog = TP_UNIT_LOG;       // a unit: 2^kUnitLog consecutive positions from a multiple of it
+constexpr uint32_t kUnit = 1u << kUnitLog;
+constexpr int kUnitQuads = (int)(kUnit / 4);     // 16-byte loads per unit
+static_assert(kColPad >= kUnit, "the padding of col[] covers the last unit of the last out-list");
+
 struct InStage {
     uint32_t* j0;
     uint32_t* jend;
@@ -298,7 +305,7 @@ __device__ __forceinline__ uint32_t upper_bound_col(const uint32_t* __restrict__
     return lo;
 }
 
-// Stage in-edge slot k (absolute record kk); returns its segment's quad count.
+// Stage in-edge slot k (absolute record kk); returns its segment's unit count.
 template <int F>
 __device__ __forceinline__ uint32_t stage_in_edge(const GraphDev& g, const SurveyArgs& a, InStage S, uint32_t k,
                                                   uint32_t kk, bool chunked, uint32_t vlo, uint32_t vhi) {
@@ -330,7 +337,7 @@ __device__ __forceinline__ uint32_t stage_in_edge(const GraphDev& g, const Surve
     S.tpq[k] = ie.ts;
     S.meta[k] = ie.meta;
     if (F & F_EXTRA) S.p[k] = p;
-    return (ok && j0 < jend) ? ((jend + 3) >> 2) - (j0 >> 2) : 0u;
+    return (ok && j0 < jend) ? ((jend + kUnit - 1) >> kUnitLog) - (j0 >> kUnitLog) : 0u;
 }
 
 // Last slot k in [lo, hi) with pp[k] <= f (pp non-decreasing, pp[lo] <= f).
@@ -343,9 +350,9 @@ __device__ __forceinline__ uint32_t seg_of(const uint32_t* pp, uint32_t lo, uint
 }
 
 #ifndef TP_UNROLL
-#define TP_UNROLL 2
+#define TP_UNROLL 1
 #endif
-constexpr int kUnroll = TP_UNROLL;  // quads each lane has in flight per chunk
+constexpr int kUnroll = TP_UNROLL;  // units each lane has in flight per chunk
 constexpr int kHitQ = 64;  // per-warp queue of hits awaiting the fold (< 32 left + 32 new)
 
 // Per-warp queue of wedge checks that hit: CSR position of (p,r), and
@@ -431,10 +438,11 @@ __device__ __forceinline__ void push_quad(const int (&pos)[4], uint32_t e0, uint
     }
 }
 
-// The calling warp checks the flat quad indices [f_begin, f_end) of the item
-// in consecutive chunks of 32*kUnroll quads: lane l takes quads f0 + 32u + l,
-// so consecutive lanes read consecutive 16-byte quads of a pivot suffix
-// (coalesced), and each probes the quad's candidates r in the table of q.
+// The calling warp checks the flat unit indices [f_begin, f_end) of the item
+// in consecutive chunks of 32*kUnroll units: lane l takes units f0 + 32u + l,
+// so consecutive lanes read consecutive 32-byte units of a pivot suffix
+// (coalesced), and each probes the unit's candidates r in the table of q, a
+// 16-byte quad at a time.
 // The in-edge slots a chunk spans are found from the previous chunk's with
 // one ballot.  Hits are queued and folded 32 at a time, one per lane.
 template <int F, class PosT>
@@ -449,14 +457,14 @@ __device__ __forceinline__ void scan_flat(const GraphDev& g, const SurveyArgs& a
     t.d_q = d_q;
     t.q = q;
     uint32_t nq = 0;   // queued hits (warp-uniform)
-    uint32_t klo = 0;  // slot holding the chunk's first quad
+    uint32_t klo = 0;  // slot holding the chunk's first unit
     {
         uint32_t kb = 0;
         if (lane == 0 && f_begin < f_end) kb = seg_of(S.pp, 0, n_in, f_begin);
         klo = __shfl_sync(0xffffffffu, kb, 0);
     }
     for (uint32_t f0 = f_begin; f0 < f_end; f0 += 32 * kUnroll) {
-        // khi: first slot after klo whose prefix passes the chunk's last quad (pp[n_in] = total)
+        // khi: first slot after klo whose prefix passes the chunk's last unit (pp[n_in] = total)
         const uint32_t fl = min(f0 + 32 * kUnroll - 1, f_end - 1);
         uint32_t khi = 0;
         for (uint32_t base = klo + 1;; base += 32) {
@@ -467,7 +475,7 @@ __device__ __forceinline__ void scan_flat(const GraphDev& g, const SurveyArgs& a
                 break;
             }
         }
-        uint4 v[kUnroll];
+        uint4 v[kUnroll][kUnitQuads];
         uint32_t e0[kUnroll], lo[kUnroll], hi[kUnroll], ks[kUnroll];
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
@@ -480,21 +488,27 @@ __device__ __forceinline__ void scan_flat(const GraphDev& g, const SurveyArgs& a
                 const uint32_t k = seg_of(S.pp, klo, khi, f);
                 const uint32_t j0 = S.j0[k];
                 ks[u] = k;
-                e0[u] = ((j0 >> 2) + (f - S.pp[k])) << 2;
+                e0[u] = ((j0 >> kUnitLog) + (f - S.pp[k])) << kUnitLog;
                 lo[u] = j0;
                 hi[u] = S.jend[k];
-                v[u] = __ldg(reinterpret_cast<const uint4*>(g.col + e0[u]));
+#pragma unroll
+                for (int c = 0; c < kUnitQuads; ++c)
+                    v[u][c] = __ldg(reinterpret_cast<const uint4*>(g.col + e0[u]) + c);
             }
         }
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
-            const uint32_t rr[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
-            bool act[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) act[i] = e0[u] + i >= lo[u] && e0[u] + i < hi[u];
-            int pos[4];
-            probe_quad(T, rr, act, pos);
-            push_quad<F>(pos, e0[u], ks[u], nq, g, a, T, S, H, t, s_tab, grec, cnt);
+            for (int c = 0; c < kUnitQuads; ++c) {
+                const uint32_t rr[4] = {v[u][c].x, v[u][c].y, v[u][c].z, v[u][c].w};
+                const uint32_t ec = e0[u] + 4 * c;
+                bool act[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) act[i] = ec + i >= lo[u] && ec + i < hi[u];
+                int pos[4];
+                probe_quad(T, rr, act, pos);
+                push_quad<F>(pos, ec, ks[u], nq, g, a, T, S, H, t, s_tab, grec, cnt);
+            }
         }
         klo = khi - 1;
     }
