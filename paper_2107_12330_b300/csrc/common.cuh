@@ -120,8 +120,8 @@ struct tripoll_graph {
     uint64_t* in_off = nullptr;
     tp::InEdge* in_edge = nullptr;
     // survey plan
-    tp::WorkItem* items_warp = nullptr;   // d+(q) <= kWarpMaxQ
-    tp::WorkItem* items_block = nullptr;  // kWarpMaxQ < d+(q) <= kBlockChunk
+    tp::WorkItem* items_warp = nullptr;   // d+(q) <= kWarpPlanQ
+    tp::WorkItem* items_block = nullptr;  // kWarpPlanQ < d+(q) <= 4 kBlockChunk
     tp::WorkItem* items_big = nullptr;    // d+(q) > kBlockChunk, chunks of kBigChunk
     uint64_t n_items_warp = 0, n_items_block = 0, n_items_big = 0;
     // statistics
@@ -137,7 +137,11 @@ struct tripoll_graph {
 
 namespace tp {
 // survey plan limits shared by the builder and the survey kernels
-constexpr uint32_t kWarpMaxQ = 64;      // middle vertices with d+(q) <= this go to the warp kernel
+constexpr uint32_t kWarpMaxQ = 64;      // entries of q's out-list a warp stages at a time
+#ifndef TP_WARP_PLAN_Q
+#define TP_WARP_PLAN_Q 128
+#endif
+constexpr uint32_t kWarpPlanQ = TP_WARP_PLAN_Q;  // middle vertices with d+(q) <= this go to the warp kernel
 constexpr uint32_t kBlockChunk = 1024;  // on-chip staged entries of q's out-list per block item
 constexpr uint32_t kBigChunk = 2048;    // the same for the large-table block kernel
 constexpr uint32_t kWarpInEdges = 64;   // in-edges per warp item

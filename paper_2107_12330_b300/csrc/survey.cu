@@ -692,35 +692,43 @@ __global__ void __launch_bounds__(kBlockThreads) survey_warp_kernel(GraphDev g, 
             qbase = b0;
             if (len == 0) continue;  // no in-window (q,r): no triangle
         }
-        T.size = view_table_size(len, g.newpos != nullptr, kWTable);
-        const uint32_t tsize = T.size;
-        __syncwarp();
-        for (uint32_t i = lane; i < tsize; i += 32) ws.key[i] = kEmpty;
-        __syncwarp();
-        table_fill<F>(g, a, T, qbase, len, lane, 32);
-        const uint32_t n_in = item.in_hi - item.in_lo;
-        uint32_t np0 = 0, np1 = 0;
-        if ((uint32_t)lane < n_in) np0 = stage_in_edge<F>(g, a, S, lane, item.in_lo + lane, false, 0u, 0u);
-        if ((uint32_t)lane + 32 < n_in)
-            np1 = stage_in_edge<F>(g, a, S, lane + 32, item.in_lo + lane + 32, false, 0u, 0u);
-        // exclusive prefix over slots 0..63 held as (lane, lane + 32)
-        uint32_t x0 = np0, x1 = np1;
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y0 = __shfl_up_sync(0xffffffffu, x0, o), y1 = __shfl_up_sync(0xffffffffu, x1, o);
-            if (lane >= o) { x0 += y0; x1 += y1; }
-        }
-        const uint32_t half = __shfl_sync(0xffffffffu, x0, 31);
-        const uint32_t total = half + __shfl_sync(0xffffffffu, x1, 31);
-        if ((uint32_t)lane < n_in) ws.pp[lane] = x0 - np0;
-        if ((uint32_t)lane + 32 < n_in) ws.pp[lane + 32] = half + x1 - np1;
-        if (lane == 0) ws.pp[n_in] = total;
-        __syncwarp();
         const uint32_t l_q = (F & F_VL) ? __ldg(&g.vl[q]) : 0u;
         const uint32_t d_q = (F & F_EXTRA) ? __ldg(&g.deg[q]) : 0u;
-        HitQueue H;
-        H.idx = ws.qidx;
-        H.pk = ws.qpk;
-        scan_flat<F>(g, a, T, S, H, n_in, 0, total, qbase, q, l_q, d_q, s_tab, grec, cnt);
+        const uint32_t n_in = item.in_hi - item.in_lo;
+        const bool chunked = len > kWarpMaxQ;
+        // the out-list is staged kWarpMaxQ entries at a time (one part unless the window
+        // leaves more in it); each part restricts the suffixes to its value range
+        for (uint32_t c0 = 0; c0 < len; c0 += kWarpMaxQ) {
+            const uint32_t clen = min(kWarpMaxQ, len - c0);
+            T.size = view_table_size(clen, g.newpos != nullptr, kWTable);
+            const uint32_t tsize = T.size;
+            __syncwarp();
+            for (uint32_t i = lane; i < tsize; i += 32) ws.key[i] = kEmpty;
+            __syncwarp();
+            table_fill<F>(g, a, T, qbase + c0, clen, lane, 32);
+            const uint32_t vlo = chunked ? __ldg(&g.col[qbase + c0]) : 0u;
+            const uint32_t vhi = chunked ? __ldg(&g.col[qbase + c0 + clen - 1]) : 0xFFFFFFFFu;
+            uint32_t np0 = 0, np1 = 0;
+            if ((uint32_t)lane < n_in) np0 = stage_in_edge<F>(g, a, S, lane, item.in_lo + lane, chunked, vlo, vhi);
+            if ((uint32_t)lane + 32 < n_in)
+                np1 = stage_in_edge<F>(g, a, S, lane + 32, item.in_lo + lane + 32, chunked, vlo, vhi);
+            // exclusive prefix over slots 0..63 held as (lane, lane + 32)
+            uint32_t x0 = np0, x1 = np1;
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y0 = __shfl_up_sync(0xffffffffu, x0, o), y1 = __shfl_up_sync(0xffffffffu, x1, o);
+                if (lane >= o) { x0 += y0; x1 += y1; }
+            }
+            const uint32_t half = __shfl_sync(0xffffffffu, x0, 31);
+            const uint32_t total = half + __shfl_sync(0xffffffffu, x1, 31);
+            if ((uint32_t)lane < n_in) ws.pp[lane] = x0 - np0;
+            if ((uint32_t)lane + 32 < n_in) ws.pp[lane + 32] = half + x1 - np1;
+            if (lane == 0) ws.pp[n_in] = total;
+            __syncwarp();
+            HitQueue H;
+            H.idx = ws.qidx;
+            H.pk = ws.qpk;
+            scan_flat<F>(g, a, T, S, H, n_in, 0, total, qbase + c0, q, l_q, d_q, s_tab, grec, cnt);
+        }
     }
     if (grec_prev) flush_count(cnt, a, s_tab, grec_prev);
     __syncthreads();
@@ -734,8 +742,8 @@ __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < 
 // Items of middle vertex q: for each part of Adj+(q) staged at once (one part
 // unless d+(q) exceeds the kernel's chunk), groups of at most `per` in-edges.
 __device__ __forceinline__ void plan_shape(uint64_t dp, uint64_t di, int& kind, uint64_t& chunk, uint64_t& per) {
-    kind = dp <= kWarpMaxQ ? 0 : (dp <= 4 * kBlockChunk ? 1 : 2);
-    chunk = kind == 0 ? kWarpMaxQ : (kind == 1 ? kBlockChunk : kBigChunk);
+    kind = dp <= kWarpPlanQ ? 0 : (dp <= 4 * kBlockChunk ? 1 : 2);
+    chunk = kind == 0 ? kWarpPlanQ : (kind == 1 ? kBlockChunk : kBigChunk);
     per = kind == 0 ? kWarpInEdges : kItemInEdges;
 }
 
