@@ -19,6 +19,7 @@
 #include <cub/cub.cuh>
 
 #include <algorithm>
+#include <utility>
 #include <vector>
 
 #include "common.cuh"
@@ -438,11 +439,13 @@ int build_impl(const uint32_t* src_h, const uint32_t* dst_h, const uint32_t* ts_
         TP_CUDA(cudaMemcpyAsync(&m, runs.as<uint64_t>() + 1, 8, cudaMemcpyDeviceToHost, s));
         TP_CUDA(cudaStreamSynchronize(s));
         if (m >= 0xFFFFFFFFull) return fail(TRIPOLL_ERR_INVALID_ARG, "more than 2^32-2 unique edges");
-        // keep the unique arrays, drop the rest
-        TP_CUDA(ukey_d.alloc(m * 8, s));
-        TP_CUDA(uval_d.alloc(m * 8, s));
-        TP_CUDA(cudaMemcpyAsync(ukey_d.ptr, ukey, m * 8, cudaMemcpyDeviceToDevice, s));
-        TP_CUDA(cudaMemcpyAsync(uval_d.ptr, uval, m * 8, cudaMemcpyDeviceToDevice, s));
+        // keep the buffers holding the unique arrays, drop the other two
+        Scratch& kk = ukey == k0.as<uint64_t>() ? k0 : k1;
+        Scratch& vv = uval == v0.as<uint64_t>() ? v0 : v1;
+        std::swap(ukey_d.ptr, kk.ptr);
+        std::swap(ukey_d.stream, kk.stream);
+        std::swap(uval_d.ptr, vv.ptr);
+        std::swap(uval_d.stream, vv.stream);
     }
     g->m = m;
 
@@ -552,8 +555,11 @@ int build_impl(const uint32_t* src_h, const uint32_t* dst_h, const uint32_t* ts_
         Scratch tmp3;
         TP_CUDA(tmp3.alloc(tb3, s));
         TP_CUDA(cub::DeviceRadixSort::SortPairs(tmp3.ptr, tb3, ckb, reb, m, 0, tbits, s));
-        if (m && reb.Current() != g->in_edge)
-            TP_CUDA(cudaMemcpyAsync(g->in_edge, reb.Current(), m * sizeof(InEdge), cudaMemcpyDeviceToDevice, s));
+        if (reb.Current() != g->in_edge) {  // the sorted records are in the second buffer: keep that one
+            void* first_buf = g->in_edge;
+            g->in_edge = reb.Current();
+            rec1.ptr = first_buf;
+        }
         // in-edge offsets from the runs of equal targets
         TP_CUDA(out_offsets(ckb.Current(), m, 0, n, first.as<uint32_t>(), cnt.as<uint32_t>(), g->in_off, tmp.ptr, tb,
                             s));
