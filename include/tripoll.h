@@ -56,7 +56,7 @@ typedef enum {
  *   TRIPOLL_CLOSURE_HIST   33 words  closing time t3 - t1 of the sorted edge
  *                                    timestamps t1 <= t2 <= t3, counted in bin
  *                                    ceil(log2(t3 - t1)); differences 0 and 1
- *                                    both land in bin 0 (Sec. 5.8, Alg. 4).
+ *                                    both land in bin 0 (Sec. 5.7, Alg. 4).
  *   TRIPOLL_VLABEL_TRIPLES Lv^3      sorted vertex-label triple a <= b <= c at
  *                                    index (a*Lv + b)*Lv + c; other entries 0.
  *   TRIPOLL_ELABEL_TRIPLES Le^3      the same over the three edge labels.
@@ -65,7 +65,7 @@ typedef enum {
  *   TRIPOLL_MAX_ELABEL     Le        Alg. 3: among triangles whose three vertex
  *                                    labels are pairwise distinct, the count per
  *                                    maximum edge label.
- *   TRIPOLL_DEGREE_TRIPLES 33^3      Sec. 5.10: sorted triple of ceil(log2 d(v))
+ *   TRIPOLL_DEGREE_TRIPLES 33^3      Sec. 5.9:  sorted triple of ceil(log2 d(v))
  *                                    of the three vertices (d = degree in the
  *                                    simple graph), indexed like the label triples.
  *   TRIPOLL_VERTEX_LOCAL   n         local triangle participation per vertex, by

@@ -6,7 +6,8 @@ imports the library: they share no code.
 
 ``survey`` returns a dict of numpy uint64 arrays (``count``, ``hist`` [33],
 ``vtri`` [Lv^3], ``etri`` [Le^3], and on request ``joint`` [33*33], ``maxel``
-[Le], ``degtri`` [33^3], ``vlocal`` [n]) plus the graph statistics of G+.  What
+[Le], ``degtri`` [33^3], ``vlocal`` [n], ``elocal`` [m], the unique edges in
+ascending (min id, max id) order) plus the graph statistics of G+.  What
 each one means is stated in ``oracle.c`` with the paper passage it follows.
 """
 from __future__ import annotations
@@ -27,7 +28,7 @@ _lib = None
 
 class _Out(ctypes.Structure):
     _fields_ = [(k, ctypes.c_void_p) for k in
-                ("count", "hist", "vtri", "etri", "joint", "maxel", "degtri", "vlocal")]
+                ("count", "hist", "vtri", "etri", "joint", "maxel", "degtri", "vlocal", "elocal")]
 
 
 class _Stats(ctypes.Structure):
@@ -91,8 +92,10 @@ def survey(src, dst, ts, elabel, vlabel, n, num_vlabels=1, num_elabels=1, t_lo=0
         res["degtri"] = np.zeros(HIST_BINS ** 3, np.uint64)
     if "vlocal" in extras:
         res["vlocal"] = np.zeros(max(n, 1), np.uint64)
+    if "elocal" in extras:  # the unique edge count is at most m_in; trimmed below
+        res["elocal"] = np.zeros(max(m_in, 1), np.uint64)
     out = _Out(*[res[k].ctypes.data if k in res else None for k in
-                 ("count", "hist", "vtri", "etri", "joint", "maxel", "degtri", "vlocal")])
+                 ("count", "hist", "vtri", "etri", "joint", "maxel", "degtri", "vlocal", "elocal")])
     st = _Stats()
     lo, hi = (0, n) if pivot_range is None else pivot_range
     rc = lib.oracle_survey(
@@ -105,6 +108,8 @@ def survey(src, dst, ts, elabel, vlabel, n, num_vlabels=1, num_elabels=1, t_lo=0
         raise MemoryError("oracle_survey: out of host memory")
     if "vlocal" in res:
         res["vlocal"] = res["vlocal"][:n]
+    if "elocal" in res:
+        res["elocal"] = res["elocal"][:int(st.m)]
     res["stats"] = dict(m=int(st.m), wedges=int(st.wedges), dplus_max=int(st.dplus_max),
                         dmax=int(st.dmax))
     return res

@@ -30,8 +30,10 @@
  *        etri[a][b][c] += 1, (a,b,c) the sorted edge labels
  *        maxel[max edge label] += 1 when the three vertex labels are pairwise
  *          distinct                                   (Alg. 3)
- *        degtri[(ceil log2 d) sorted triple] += 1     (Sec. 5.10)
+ *        degtri[(ceil log2 d) sorted triple] += 1     (Sec. 5.9)
  *        vlocal[p], vlocal[q], vlocal[r] += 1         (local counts, Sec. 5.3)
+ *        elocal[pq], elocal[pr], elocal[qr] += 1      (local edge counts, Sec. 5.3;
+ *          edges numbered in (min id, max id) order)
  *   Output arrays the caller passes as NULL are skipped.
  *
  * The pivots can be restricted to a range of positions in the <+ order, so
@@ -53,6 +55,7 @@ typedef struct {
     uint64_t* maxel;  /* [Le] */
     uint64_t* degtri; /* [33^3] */
     uint64_t* vlocal; /* [n], by input vertex id */
+    uint64_t* elocal; /* [m], by unique edge in ascending (min id, max id) order */
 } oracle_out;
 
 typedef struct {
@@ -196,6 +199,11 @@ static void fold(const work_t* w, uint32_t p, uint32_t q, uint32_t r, uint64_t e
         o->vlocal[p] += 1;
         o->vlocal[q] += 1;
         o->vlocal[r] += 1;
+    }
+    if (o->elocal) {
+        o->elocal[e_pq] += 1;
+        o->elocal[e_pr] += 1;
+        o->elocal[e_qr] += 1;
     }
 }
 
@@ -369,10 +377,12 @@ int oracle_survey(const uint32_t* src, const uint32_t* dst, const uint32_t* ts, 
             w->out.maxel = out->maxel ? (uint64_t*)calloc(Le, 8) : NULL;
             w->out.degtri = out->degtri ? (uint64_t*)calloc(dt3, 8) : NULL;
             w->out.vlocal = out->vlocal ? (uint64_t*)calloc((size_t)n + 1, 8) : NULL;
+            w->out.elocal = out->elocal ? (uint64_t*)calloc((size_t)m + 1, 8) : NULL;
             if ((out->count && !w->out.count) || (out->hist && !w->out.hist) ||
                 (out->vtri && !w->out.vtri) || (out->etri && !w->out.etri) ||
                 (out->joint && !w->out.joint) || (out->maxel && !w->out.maxel) ||
-                (out->degtri && !w->out.degtri) || (out->vlocal && !w->out.vlocal))
+                (out->degtri && !w->out.degtri) || (out->vlocal && !w->out.vlocal) ||
+                (out->elocal && !w->out.elocal))
                 rc = -2;
         }
     }
@@ -390,12 +400,14 @@ int oracle_survey(const uint32_t* src, const uint32_t* dst, const uint32_t* ts, 
             add_into(out->maxel, o->maxel, Le);
             add_into(out->degtri, o->degtri, dt3);
             add_into(out->vlocal, o->vlocal, n);
+            add_into(out->elocal, o->elocal, m);
         }
     }
     for (int t = 1; works && t < threads; ++t) {
         oracle_out* o = &works[t].out;
         free(o->count); free(o->hist); free(o->vtri); free(o->etri); free(o->joint);
         free(o->maxel); free(o->degtri); free(o->vlocal);
+        free(o->elocal);
     }
     free(works); free(tids);
     free(eu); free(ev); free(ets); free(eel); free(deg); free(vertex_at); free(pos_of);

@@ -16,7 +16,7 @@ import pytest
 import oracle
 import synth
 
-ALL_EXTRAS = ("joint", "maxel", "degtri", "vlocal")
+ALL_EXTRAS = ("joint", "maxel", "degtri", "vlocal", "elocal")
 
 
 def run(src, dst, ts, el, vl, n, Lv, Le, **kw):
@@ -48,8 +48,9 @@ def brute_force(src, dst, ts, el, vl, n, Lv, Le, t_lo=0, t_hi=0xFFFFFFFF):
         deg[u] += 1
         deg[v] += 1
     lab = [int(x) for x in vl] if vl is not None else [0] * n
+    index = {key: i for i, key in enumerate(sorted(edges))}  # unique edges in (min id, max id) order
     res = {"count": 0, "hist": [0] * 33, "vtri": [0] * Lv ** 3, "etri": [0] * Le ** 3, "joint": [0] * 33 * 33,
-           "maxel": [0] * Le, "degtri": [0] * 33 ** 3, "vlocal": [0] * n}
+           "maxel": [0] * Le, "degtri": [0] * 33 ** 3, "vlocal": [0] * n, "elocal": [0] * len(edges)}
     for x, y, z in itertools.combinations(range(n), 3):
         if (x, y) in edges and (x, z) in edges and (y, z) in edges:
             (t1, e1), (t2, e2), (t3, e3) = edges[(x, y)], edges[(x, z)], edges[(y, z)]
@@ -69,6 +70,8 @@ def brute_force(src, dst, ts, el, vl, n, Lv, Le, t_lo=0, t_hi=0xFFFFFFFF):
             res["degtri"][(da * 33 + db) * 33 + dc] += 1
             for w in (x, y, z):
                 res["vlocal"][w] += 1
+            for key in ((x, y), (x, z), (y, z)):
+                res["elocal"][index[key]] += 1
     return res
 
 
@@ -106,7 +109,7 @@ def test_single_triangle_worked_example():
                                       (6, 30, 200), (7, 40, 700)])
 def test_brute_force_all_tables(seed, n, m):
     g = synth.tiny_random_graph(seed, n, m, ts_bits=5, num_vlabels=3, num_elabels=4)
-    r = oracle.survey_graph(g)
+    r = oracle.survey_graph(g, extras=ALL_EXTRAS)
     b = brute_force(g.src, g.dst, g.ts, g.elabel, g.vlabel, n, 3, 4)
     same(r, b)
 
@@ -114,7 +117,8 @@ def test_brute_force_all_tables(seed, n, m):
 @pytest.mark.parametrize("window", [(3, 20), (0, 0), (31, 31), (10, 11)])
 def test_brute_force_windows(window):
     g = synth.tiny_random_graph(17, 20, 250, ts_bits=5, num_vlabels=2, num_elabels=2)
-    r = oracle.survey(g.src, g.dst, g.ts, g.elabel, g.vlabel, g.n, 2, 2, t_lo=window[0], t_hi=window[1])
+    r = oracle.survey(g.src, g.dst, g.ts, g.elabel, g.vlabel, g.n, 2, 2, t_lo=window[0], t_hi=window[1],
+                      extras=ALL_EXTRAS)
     same(r, brute_force(g.src, g.dst, g.ts, g.elabel, g.vlabel, g.n, 2, 2, *window))
 
 
@@ -140,9 +144,10 @@ def test_complete_graph_over_several_thread_blocks():
     """K_600 with 4 threads: pivots fall in three blocks of 256, so every per-thread table is merged."""
     n = 600
     iu = np.triu_indices(n, 1)
-    r = run(iu[0], iu[1], np.arange(len(iu[0])), None, None, n, 1, 1, threads=4)
+    r = run(iu[0], iu[1], np.arange(len(iu[0])), None, None, n, 1, 1, threads=4, extras=ALL_EXTRAS)
     assert int(r["count"][0]) == math.comb(n, 3)
     assert r["vlocal"].tolist() == [math.comb(n - 1, 2)] * n
+    assert r["elocal"].tolist() == [n - 2] * math.comb(n, 2)  # every edge closes with each of the other n - 2
     assert int(r["degtri"][(10 * 33 + 10) * 33 + 10]) == math.comb(n, 3)  # degree 599 -> bin 10
 
 
@@ -169,12 +174,13 @@ def test_count_equals_trace_of_a_cubed_over_six():
 
 def test_table_sums_and_marginals():
     g = synth.rmat_graph(10, 16, 2, ts_bits=16, num_vlabels=4, num_elabels=3)
-    r = oracle.survey_graph(g)
+    r = oracle.survey_graph(g, extras=ALL_EXTRAS)
     c = int(r["count"][0])
     assert c > 0
     for k in ("hist", "vtri", "etri", "joint", "degtri"):
         assert int(r[k].sum()) == c, k
     assert int(r["vlocal"].sum()) == 3 * c
+    assert int(r["elocal"].sum()) == 3 * c
     assert np.array_equal(r["joint"].reshape(33, 33).sum(axis=0), r["hist"])  # marginal over open time
     assert int(r["maxel"].sum()) <= c
 

@@ -66,6 +66,8 @@ MUTANTS = [
     ("wedges_formula", "wedges += d * (d ? d - 1 : 0) / 2;", "wedges += d * d / 2;"),
     # thread blocks overlap
     ("threads_overlap", "% w->stride != w->t) continue;", "% w->stride > w->t) continue;"),
+    # per-edge participation credits (p,r) to (p,q)
+    ("elocal_wrong_edge", "o->elocal[e_pr] += 1;", "o->elocal[e_pq] += 1;"),
     # per-thread vertex tables merged short by one
     ("merge_vlocal_short", "add_into(out->vlocal, o->vlocal, n);", "add_into(out->vlocal, o->vlocal, n ? n - 1 : 0);"),
 ]
