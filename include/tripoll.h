@@ -70,6 +70,12 @@ typedef enum {
  *                                    simple graph), indexed like the label triples.
  *   TRIPOLL_VERTEX_LOCAL   n         local triangle participation per vertex, by
  *                                    input vertex id (Sec. 5.3).
+ *   TRIPOLL_EDGE_LOCAL     m         local triangle participation per edge of G+
+ *                                    (Sec. 5.3), by the edge's CSR position:
+ *                                    word off[p] + i is the i-th out-edge of the
+ *                                    vertex at position p, whose endpoints are
+ *                                    order[p] and order[col[off[p] + i]] (see
+ *                                    tripoll_graph_export); m = num_edges.
  *
  * A triangle is surveyed iff its three edge timestamps all lie in the inclusive
  * window [t_lo, t_hi]; [0, 0xFFFFFFFF] surveys every triangle.  This equals
@@ -82,9 +88,10 @@ enum {
     TRIPOLL_OPEN_CLOSE_HIST = 16,
     TRIPOLL_MAX_ELABEL = 32,
     TRIPOLL_DEGREE_TRIPLES = 64,
-    TRIPOLL_VERTEX_LOCAL = 128
+    TRIPOLL_VERTEX_LOCAL = 128,
+    TRIPOLL_EDGE_LOCAL = 256
 };
-#define TRIPOLL_ALL_KINDS 255u
+#define TRIPOLL_ALL_KINDS 511u
 #define TRIPOLL_HIST_BINS 33u
 
 /* Statistics of a built graph (G+ of Sec. 3).  Sizes are counts, not bytes. */
@@ -137,9 +144,10 @@ int tripoll_batch_create(const uint32_t* src, const uint32_t* dst, const uint32_
                          tripoll_graph_t* out);
 
 /* Number of uint64 words of a result for kind_mask (TRIPOLL_VERTEX_LOCAL adds
- * num_vertices words, the others fixed sizes listed above). */
+ * num_vertices words, TRIPOLL_EDGE_LOCAL num_edges -- the unique edges of G+,
+ * tripoll_graph_stats' num_edges --, the others fixed sizes listed above). */
 uint64_t tripoll_result_words(uint32_t kind_mask, uint32_t num_vlabels, uint32_t num_elabels,
-                              uint64_t num_vertices);
+                              uint64_t num_vertices, uint64_t num_edges);
 
 /* Run one survey (Alg. 1 with the fold of the requested kinds) over every
  * triangle of g whose edge timestamps lie in [t_lo, t_hi].  A window other

@@ -34,7 +34,8 @@ TRIPOLL_OPEN_CLOSE_HIST = 16
 TRIPOLL_MAX_ELABEL = 32
 TRIPOLL_DEGREE_TRIPLES = 64
 TRIPOLL_VERTEX_LOCAL = 128
-TRIPOLL_ALL_KINDS = 255
+TRIPOLL_EDGE_LOCAL = 256
+TRIPOLL_ALL_KINDS = 511
 TRIPOLL_HIST_BINS = 33
 FULL_WINDOW = (0, 0xFFFFFFFF)
 
@@ -82,7 +83,7 @@ def load_library(path: str = LIB_PATH):
     pvp = ctypes.POINTER(ctypes.c_void_p)
     lib.tripoll_graph_create.argtypes = [vp, vp, vp, vp, u64, vp, u32, u32, u32, vp, pvp]
     lib.tripoll_batch_create.argtypes = [vp, vp, vp, vp, vp, vp, vp, u32, u32, u32, vp, pvp]
-    lib.tripoll_result_words.argtypes = [u32, u32, u32, u64]
+    lib.tripoll_result_words.argtypes = [u32, u32, u32, u64, u64]
     lib.tripoll_result_words.restype = u64
     lib.tripoll_survey.argtypes = [vp, u32, u32, u32, vp, vp]
     lib.tripoll_survey_range.argtypes = [vp, u32, u32, u32, u64, u64, vp, vp]
@@ -181,8 +182,8 @@ def tripoll_batch_create(src, dst, ts, elabel, edge_offsets, vlabel, num_vertice
     return out.value
 
 
-def tripoll_result_words(kind_mask, num_vlabels, num_elabels, num_vertices=0):
-    return int(load_library().tripoll_result_words(kind_mask, num_vlabels, num_elabels, num_vertices))
+def tripoll_result_words(kind_mask, num_vlabels, num_elabels, num_vertices=0, num_edges=0):
+    return int(load_library().tripoll_result_words(kind_mask, num_vlabels, num_elabels, num_vertices, num_edges))
 
 
 def tripoll_survey(g, kind_mask, t_lo, t_hi, result, stream=None):
@@ -288,14 +289,14 @@ def tripoll_last_error():
     return load_library().tripoll_last_error().decode()
 
 
-def split_result(vec, kind_mask, num_vlabels, num_elabels, num_vertices=0):
+def split_result(vec, kind_mask, num_vlabels, num_elabels, num_vertices=0, num_edges=0):
     """Views of the tables in one result record, by kind name (layout of tripoll.h)."""
     out, o = {}, 0
     sizes = [("count", TRIPOLL_COUNT, 1), ("hist", TRIPOLL_CLOSURE_HIST, TRIPOLL_HIST_BINS),
              ("vtri", TRIPOLL_VLABEL_TRIPLES, num_vlabels ** 3), ("etri", TRIPOLL_ELABEL_TRIPLES, num_elabels ** 3),
              ("joint", TRIPOLL_OPEN_CLOSE_HIST, TRIPOLL_HIST_BINS ** 2), ("maxel", TRIPOLL_MAX_ELABEL, num_elabels),
              ("degtri", TRIPOLL_DEGREE_TRIPLES, TRIPOLL_HIST_BINS ** 3),
-             ("vlocal", TRIPOLL_VERTEX_LOCAL, num_vertices)]
+             ("vlocal", TRIPOLL_VERTEX_LOCAL, num_vertices), ("elocal", TRIPOLL_EDGE_LOCAL, num_edges)]
     for name, bit, size in sizes:
         if kind_mask & bit:
             out[name] = vec[o:o + size]

@@ -55,7 +55,7 @@ int check_survey_args(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uin
     if (t_lo > t_hi) return fail(TRIPOLL_ERR_INVALID_ARG, "t_lo > t_hi");
     if ((kinds & (TRIPOLL_ELABEL_TRIPLES | TRIPOLL_MAX_ELABEL)) && !g->has_el)
         return fail(TRIPOLL_ERR_NO_EDGE_LABELS, "edge-label survey on a graph without edge labels");
-    if ((kinds & TRIPOLL_VERTEX_LOCAL) && g->graph_of)
+    if ((kinds & (TRIPOLL_VERTEX_LOCAL | TRIPOLL_EDGE_LOCAL)) && g->graph_of)
         return fail(TRIPOLL_ERR_INVALID_ARG, "local counts are not available for batched graphs");
     return TRIPOLL_OK;
 }
@@ -65,7 +65,7 @@ int survey_into(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_t 
                 uint64_t* result, cudaStream_t s) {
     int rc = check_survey_args(g, kinds, t_lo, t_hi, result);
     if (rc) return rc;
-    const Layout lay = make_layout(kinds, g->Lv, g->Le, g->n);
+    const Layout lay = make_layout(kinds, g->Lv, g->Le, g->n, g->m);
     const uint64_t words = lay.words * g->num_graphs;
     const bool dev_result = is_device_pointer(result);
     Scratch acc, ctr;
@@ -168,8 +168,9 @@ extern "C" const char* tripoll_last_error(void) { return g_last_error.c_str(); }
 extern "C" uint64_t tripoll_launch_count(void) { return g_launches.load(); }
 
 extern "C" uint64_t tripoll_result_words(uint32_t kind_mask, uint32_t num_vlabels, uint32_t num_elabels,
-                                         uint64_t num_vertices) {
-    return make_layout(kind_mask, num_vlabels ? num_vlabels : 1, num_elabels ? num_elabels : 1, num_vertices).words;
+                                         uint64_t num_vertices, uint64_t num_edges) {
+    return make_layout(kind_mask, num_vlabels ? num_vlabels : 1, num_elabels ? num_elabels : 1, num_vertices,
+                       num_edges).words;
 }
 
 extern "C" int tripoll_survey(tripoll_graph_t g, uint32_t kind_mask, uint32_t t_lo, uint32_t t_hi, uint64_t* result,

@@ -95,6 +95,7 @@ struct GraphDev {
     // the number of such edges before CSR position e of G+; off, in_off and
     // in_edge stay those of G+ and are translated through newpos.
     const uint32_t* newpos = nullptr;   // [m+1] or null
+    const uint32_t* vorig = nullptr;    // [m] CSR position in G+ of each view entry (per-edge counts only)
 };
 
 }  // namespace tp
@@ -153,10 +154,10 @@ constexpr uint32_t kColPad = 8;         // col[] entries past m (0xFFFFFFFF) for
 struct Layout {
     uint32_t o_count = ~0u, o_hist = ~0u, o_vtri = ~0u, o_etri = ~0u, o_joint = ~0u, o_maxel = ~0u,
              o_degtri = ~0u;
-    uint64_t o_vlocal = ~0ull;
+    uint64_t o_vlocal = ~0ull, o_elocal = ~0ull;
     uint64_t words = 0;
 };
-Layout make_layout(uint32_t kinds, uint32_t Lv, uint32_t Le, uint64_t n);
+Layout make_layout(uint32_t kinds, uint32_t Lv, uint32_t Le, uint64_t n, uint64_t m);
 
 int build_plan(tripoll_graph* g, cudaStream_t s);
 // Launch the survey kernels accumulating into `acc` (zeroed by the caller);
@@ -167,7 +168,7 @@ int launch_survey(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_
                   uint64_t p_hi, unsigned long long* acc, uint32_t* counters, cudaStream_t s,
                   bool window_view = true);
 // Device scratch the window view of g takes for [t_lo, t_hi] (0 for the full window).
-uint64_t window_view_bytes(const tripoll_graph* g, uint32_t t_lo, uint32_t t_hi);
+uint64_t window_view_bytes(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_t t_hi);
 int check_survey_args(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_t t_hi, const void* result);
 void free_graph_arrays(tripoll_graph* g);
 }  // namespace tp

@@ -193,7 +193,7 @@ extern "C" int tripoll_server_submit(tripoll_server_t s, uint32_t slot, uint32_t
     r->kinds = kind_mask;
     r->t_lo = t_lo;
     r->t_hi = t_hi;
-    r->words = make_layout(kind_mask, g->Lv, g->Le, g->n).words * g->num_graphs;
+    r->words = make_layout(kind_mask, g->Lv, g->Le, g->n, g->m).words * g->num_graphs;
     r->bytes = r->words * 8 + 16;
     r->server = s;
     if (r->bytes > s->cap) {
@@ -201,7 +201,7 @@ extern "C" int tripoll_server_submit(tripoll_server_t s, uint32_t slot, uint32_t
         return fail(TRIPOLL_ERR_NO_MEMORY, "request needs more scratch than the server budget");
     }
     // the window view when the budget holds it too, else out-of-window edges are skipped in place
-    const uint64_t vb = window_view_bytes(g, t_lo, t_hi);
+    const uint64_t vb = window_view_bytes(g, kind_mask, t_lo, t_hi);
     r->view = vb > 0 && r->bytes + vb <= s->cap;
     if (r->view) r->bytes += vb;
     {  // pinned result buffer from the pool

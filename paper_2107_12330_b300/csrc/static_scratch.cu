@@ -52,7 +52,7 @@ extern "C" int tripoll_survey_static(tripoll_graph_t g, uint32_t kind_mask, uint
                                      uint64_t* result, void* cuda_stream) {
     int rc = check_survey_args(g, kind_mask, t_lo, t_hi, result);
     if (rc) return rc;
-    const uint64_t words = make_layout(kind_mask, g->Lv, g->Le, g->n).words * g->num_graphs;
+    const uint64_t words = make_layout(kind_mask, g->Lv, g->Le, g->n, g->m).words * g->num_graphs;
     const uint64_t record_bytes = (words * 8 + 255) / 256 * 256;
     if (record_bytes + kCounterBytes > kStaticScratchBytes)
         return fail(TRIPOLL_ERR_NO_MEMORY, "survey result of " + std::to_string(words * 8) +

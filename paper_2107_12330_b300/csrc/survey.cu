@@ -41,7 +41,7 @@
 
 namespace tp {
 
-Layout make_layout(uint32_t kinds, uint32_t Lv, uint32_t Le, uint64_t n) {
+Layout make_layout(uint32_t kinds, uint32_t Lv, uint32_t Le, uint64_t n, uint64_t m) {
     Layout L;
     uint64_t w = 0;
     if (kinds & TRIPOLL_COUNT) { L.o_count = (uint32_t)w; w += 1; }
@@ -55,6 +55,7 @@ Layout make_layout(uint32_t kinds, uint32_t Lv, uint32_t Le, uint64_t n) {
         w += (uint64_t)TRIPOLL_HIST_BINS * TRIPOLL_HIST_BINS * TRIPOLL_HIST_BINS;
     }
     if (kinds & TRIPOLL_VERTEX_LOCAL) { L.o_vlocal = w; w += n; }
+    if (kinds & TRIPOLL_EDGE_LOCAL) { L.o_elocal = w; w += m; }
     L.words = w;
     return L;
 }
@@ -123,6 +124,8 @@ struct TriMeta {
     uint32_t l_p, l_q, l_r;     // vertex labels
     uint32_t d_p, d_q, d_r;     // degrees (F_EXTRA)
     uint32_t p, q, r;           // positions (F_EXTRA local counts)
+    uint32_t x_pq, x_pr, x_qr;  // CSR positions of the three edges in G+ (F_EXTRA edge counts)
+    uint32_t qbase;             // CSR position (in the surveyed arrays) of the staged part of Adj+(q)
 };
 
 // Fold the lanes with `keep` set (called by the whole warp).
@@ -163,6 +166,11 @@ __device__ __forceinline__ void fold_warp(bool keep, const TriMeta& t, const Sur
             atomicAdd(&grec[L.o_vlocal + order[t.p]], 1ull);
             atomicAdd(&grec[L.o_vlocal + order[t.q]], 1ull);
             atomicAdd(&grec[L.o_vlocal + order[t.r]], 1ull);
+        }
+        if (L.o_elocal != ~0ull) {
+            atomicAdd(&grec[L.o_elocal + t.x_pq], 1ull);
+            atomicAdd(&grec[L.o_elocal + t.x_pr], 1ull);
+            atomicAdd(&grec[L.o_elocal + t.x_qr], 1ull);
         }
     }
 }
@@ -293,6 +301,7 @@ struct InStage {
     uint32_t* tpq;
     uint32_t* meta;
     uint32_t* p;
+    uint32_t* e;   // CSR position of (p,q) in G+ (F_EXTRA)
     uint32_t* pp;  // [n_in + 1]
 };
 
@@ -336,7 +345,10 @@ __device__ __forceinline__ uint32_t stage_in_edge(const GraphDev& g, const Surve
     S.jend[k] = jend;
     S.tpq[k] = ie.ts;
     S.meta[k] = ie.meta;
-    if (F & F_EXTRA) S.p[k] = p;
+    if (F & F_EXTRA) {
+        S.p[k] = p;
+        S.e[k] = ie.e;
+    }
     return (ok && j0 < jend) ? ((jend + kUnit - 1) >> kUnitLog) - (j0 >> kUnitLog) : 0u;
 }
 
@@ -390,6 +402,10 @@ __device__ __forceinline__ void fold_queue(const GraphDev& g, const SurveyArgs& 
             t.p = S.p[k];
             t.d_p = __ldg(&g.deg[t.p]);
             t.d_r = T.deg[pos];
+            // positions in G+ of (p,r) and (q,r): through the window view's map when surveying one
+            t.x_pq = S.e[k];
+            t.x_pr = g.vorig ? __ldg(&g.vorig[idx]) : idx;
+            t.x_qr = g.vorig ? __ldg(&g.vorig[t.qbase + pos]) : t.qbase + pos;
         }
     }
     fold_warp<F>(keep, t, a, s_tab, grec, cnt, g.order);
@@ -456,6 +472,7 @@ __device__ __forceinline__ void scan_flat(const GraphDev& g, const SurveyArgs& a
     t.l_q = l_q;
     t.d_q = d_q;
     t.q = q;
+    t.qbase = qbase;
     uint32_t nq = 0;   // queued hits (warp-uniform)
     uint32_t klo = 0;  // slot holding the chunk's first unit
     {
@@ -543,7 +560,7 @@ template <int F, uint32_t CHUNK>
 constexpr size_t block_smem_fixed() {
     return kWarps * kHitQ * 8 + kTableFactor * CHUNK * 4 + CHUNK * 4 * ((F & F_EXTRA) ? 2 : 1) +
            kTableFactor * CHUNK * 2 +
-           CHUNK * (((F & F_EL) ? 1 : 0) + ((F & F_VL) ? 1 : 0)) + kBlockInEdges * 4 * ((F & F_EXTRA) ? 5 : 4) +
+           CHUNK * (((F & F_EL) ? 1 : 0) + ((F & F_VL) ? 1 : 0)) + kBlockInEdges * 4 * ((F & F_EXTRA) ? 6 : 4) +
            (kBlockInEdges + 1) * 4;
 }
 
@@ -570,7 +587,8 @@ __global__ void __launch_bounds__(kBlockThreads, CHUNK <= kBlockChunk ? 5 : 3)
     S.tpq = S.jend + kBlockInEdges;
     S.meta = S.tpq + kBlockInEdges;
     S.p = S.meta + kBlockInEdges;  // present only with F_EXTRA
-    S.pp = S.p + ((F & F_EXTRA) ? kBlockInEdges : 0);
+    S.e = S.p + ((F & F_EXTRA) ? kBlockInEdges : 0);  // present only with F_EXTRA
+    S.pp = S.e + ((F & F_EXTRA) ? kBlockInEdges : 0);
     uint32_t* hq = S.pp + kBlockInEdges + 1;
     HitQueue H;
     H.idx = hq + (threadIdx.x >> 5) * 2 * kHitQ;
@@ -647,6 +665,7 @@ struct __align__(16) WarpSmem {
     uint32_t ts[kWarpMaxQ];
     uint32_t deg[kWarpMaxQ];
     uint32_t j0[kWarpInEdges], jend[kWarpInEdges], tpq[kWarpInEdges], meta[kWarpInEdges], p[kWarpInEdges];
+    uint32_t e[kWarpInEdges];
     uint32_t pp[kWarpInEdges + 1];
     uint32_t qidx[kHitQ], qpk[kHitQ];
     uint8_t pos[kWTable];
@@ -667,7 +686,7 @@ __global__ void __launch_bounds__(kBlockThreads) survey_warp_kernel(GraphDev g, 
     QTable<uint8_t> T;
     T.key = ws.key; T.pos = ws.pos; T.ts = ws.ts; T.deg = ws.deg; T.el = ws.el; T.vl = ws.vl;
     InStage S;
-    S.j0 = ws.j0; S.jend = ws.jend; S.tpq = ws.tpq; S.meta = ws.meta; S.p = ws.p; S.pp = ws.pp;
+    S.j0 = ws.j0; S.jend = ws.jend; S.tpq = ws.tpq; S.meta = ws.meta; S.p = ws.p; S.e = ws.e; S.pp = ws.pp;
     unsigned long long cnt = 0;
     unsigned long long* grec_prev = nullptr;
 
@@ -879,7 +898,7 @@ struct InWindow {
 __global__ void window_view_kernel(const uint32_t* __restrict__ col, const uint32_t* __restrict__ ts,
                                    const uint8_t* __restrict__ el, const uint32_t* __restrict__ newpos, uint64_t m,
                                    uint32_t lo, uint32_t hi, uint32_t* __restrict__ vcol, uint32_t* __restrict__ vts,
-                                   uint8_t* __restrict__ vel) {
+                                   uint8_t* __restrict__ vel, uint32_t* __restrict__ vorig) {
     for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < m; e += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t t = ts[e];
         if (t < lo || t > hi) continue;
@@ -887,6 +906,7 @@ __global__ void window_view_kernel(const uint32_t* __restrict__ col, const uint3
         vcol[p] = col[e];
         vts[p] = t;
         if (el) vel[p] = el[e];
+        if (vorig) vorig[p] = (uint32_t)e;
     }
 }
 
@@ -939,18 +959,18 @@ int build_plan(tripoll_graph* g, cudaStream_t s) {
     return TRIPOLL_OK;
 }
 
-uint64_t window_view_bytes(const tripoll_graph* g, uint32_t t_lo, uint32_t t_hi) {
+uint64_t window_view_bytes(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_t t_hi) {
     if ((t_lo == 0 && t_hi == 0xFFFFFFFFu) || !g->m) return 0;
     const uint64_t m = g->m;
     const uint64_t r = 256;  // pool rounding per allocation
     return (m + 1) * 4 + r + 2 * ((m + kColPad) * 4 + r) + (g->el ? m + kColPad + r : 0) +
-           window_scan_bytes(m) + r;
+           ((kinds & TRIPOLL_EDGE_LOCAL) ? m * 4 + r : 0) + window_scan_bytes(m) + r;
 }
 
 // Launch the survey kernels accumulating into `acc` (zeroed by the caller).
 int launch_survey(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_t t_hi, uint64_t p_lo, uint64_t p_hi,
                   unsigned long long* acc, uint32_t* counters, cudaStream_t s, bool window_view) {
-    const Layout lay = make_layout(kinds, g->Lv, g->Le, g->n);
+    const Layout lay = make_layout(kinds, g->Lv, g->Le, g->n, g->m);
     SurveyArgs a;
     a.kinds = kinds;
     a.t_lo = t_lo;
@@ -974,7 +994,8 @@ int launch_survey(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_
     a.out = acc;
     a.counters = counters;
     // record prefix mirrored on chip: the tables that fit, never the local counts
-    uint64_t sw = lay.o_vlocal != ~0ull ? lay.o_vlocal : lay.words;
+    uint64_t sw = std::min(lay.o_vlocal, lay.o_elocal);
+    if (sw == ~0ull) sw = lay.words;
     if (g->graph_of) sw = 0;
     a.s_words = (uint32_t)std::min<uint64_t>(sw, kSharedTableWords);
     const bool window = !(t_lo == 0 && t_hi == 0xFFFFFFFFu);
@@ -982,19 +1003,21 @@ int launch_survey(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_
     if (window || (kinds & (TRIPOLL_CLOSURE_HIST | TRIPOLL_OPEN_CLOSE_HIST))) F |= F_TS;
     if (kinds & (TRIPOLL_ELABEL_TRIPLES | TRIPOLL_MAX_ELABEL)) F |= F_EL;
     if (kinds & (TRIPOLL_VLABEL_TRIPLES | TRIPOLL_MAX_ELABEL)) F |= F_VL;
-    if (kinds & (TRIPOLL_OPEN_CLOSE_HIST | TRIPOLL_MAX_ELABEL | TRIPOLL_DEGREE_TRIPLES | TRIPOLL_VERTEX_LOCAL))
+    if (kinds & (TRIPOLL_OPEN_CLOSE_HIST | TRIPOLL_MAX_ELABEL | TRIPOLL_DEGREE_TRIPLES | TRIPOLL_VERTEX_LOCAL |
+                 TRIPOLL_EDGE_LOCAL))
         F |= F_EXTRA | F_TS;
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
     TP_CUDA(cudaMemsetAsync(counters, 0, 16, s));
     GraphDev gd = g->dev();
-    Scratch vpos, vcol, vts, vel, vtmp;  // released (stream-ordered) after the survey kernels
+    Scratch vpos, vcol, vts, vel, vorig, vtmp;  // released (stream-ordered) after the survey kernels
     if (window && window_view && g->m) {
         const uint64_t m = g->m;
         TP_CUDA(vpos.alloc((m + 1) * 4, s));
         TP_CUDA(vcol.alloc((m + kColPad) * 4, s));
         TP_CUDA(vts.alloc((m + kColPad) * 4, s));
         if (g->el) TP_CUDA(vel.alloc(m + kColPad, s));
+        if (kinds & TRIPOLL_EDGE_LOCAL) TP_CUDA(vorig.alloc(m * 4, s));
         auto flags = thrust::make_transform_iterator(thrust::counting_iterator<uint64_t>(0),
                                                      InWindow{g->ts, m, t_lo, t_hi});
         size_t tb = window_scan_bytes(m);
@@ -1002,12 +1025,14 @@ int launch_survey(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_
         TP_CUDA(cub::DeviceScan::ExclusiveSum(vtmp.ptr, tb, flags, vpos.as<uint32_t>(), m + 1, s));
         window_view_kernel<<<grid_n(m), 256, 0, s>>>(g->col, g->ts, g->el, vpos.as<uint32_t>(), m, t_lo, t_hi,
                                                      vcol.as<uint32_t>(), vts.as<uint32_t>(),
-                                                     g->el ? vel.as<uint8_t>() : nullptr); ::tp::note_launch();
+                                                     g->el ? vel.as<uint8_t>() : nullptr,
+                                                     vorig.as<uint32_t>()); ::tp::note_launch();
         TP_CUDA(cudaGetLastError());
         gd.col = vcol.as<uint32_t>();
         gd.ts = vts.as<uint32_t>();
         gd.el = g->el ? vel.as<uint8_t>() : nullptr;
         gd.newpos = vpos.as<uint32_t>();
+        gd.vorig = vorig.as<uint32_t>();
     }
     kLaunch[F](g, gd, a, s, sms);
     TP_CUDA(cudaGetLastError());

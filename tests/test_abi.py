@@ -31,7 +31,8 @@ def test_result_words_layout():
     assert tp.tripoll_result_words(tp.TRIPOLL_CLOSURE_HIST, 4, 8) == 33
     assert tp.tripoll_result_words(1 | 2 | 4, 4, 1) == 1 + 33 + 64
     assert tp.tripoll_result_words(2 | 8, 16, 8) == 33 + 512
-    assert tp.tripoll_result_words(tp.TRIPOLL_ALL_KINDS, 2, 3, 10) == 1 + 33 + 8 + 27 + 33 * 33 + 3 + 33 ** 3 + 10
+    assert tp.tripoll_result_words(tp.TRIPOLL_ALL_KINDS, 2, 3, 10, 7) == 1 + 33 + 8 + 27 + 33 * 33 + 3 + 33 ** 3 + 10 + 7
+    assert tp.tripoll_result_words(tp.TRIPOLL_EDGE_LOCAL, 1, 1, 10, 7) == 7
 
 
 def test_status_strings():

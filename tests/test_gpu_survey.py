@@ -8,7 +8,7 @@ import pytest
 
 import synth
 import paper_2107_12330_b300 as tp
-from gpu_util import assert_equal_tables, build, oracle_vector, survey
+from gpu_util import assert_equal_tables, build, oracle_vector, survey, words
 
 pytestmark = pytest.mark.gpu
 
@@ -85,7 +85,26 @@ def test_complete_graph_long_out_lists():
     assert int(got[0]) == n * (n - 1) * (n - 2) // 6
     # a window: the chunks' value ranges come from their in-window entries only
     check(g, ALL & ~tp.TRIPOLL_VERTEX_LOCAL, window=(1 << 14, 3 << 14))
-    check(g, tp.TRIPOLL_COUNT | tp.TRIPOLL_VERTEX_LOCAL, window=(0, 1 << 12))
+    check(g, tp.TRIPOLL_COUNT | tp.TRIPOLL_VERTEX_LOCAL | tp.TRIPOLL_EDGE_LOCAL, window=(0, 1 << 12))
+
+
+def test_edge_local_counts_view_in_place_and_shards():
+    """Per-edge participation through the window view, in place (full window), and as pivot-range shards."""
+    g = synth.rmat(13, 3)
+    kinds = tp.TRIPOLL_COUNT | tp.TRIPOLL_VERTEX_LOCAL | tp.TRIPOLL_EDGE_LOCAL
+    check(g, kinds)
+    full = check(g, kinds | tp.TRIPOLL_CLOSURE_HIST, window=(0, 0xFFFFFFFF))
+    m = len(full) - words((kinds | tp.TRIPOLL_CLOSURE_HIST) & ~tp.TRIPOLL_EDGE_LOCAL, g)
+    assert int(full[-m:].sum()) == 3 * int(full[0])
+    h = build(g)
+    try:
+        bounds = tp.tripoll_partition_pivots(h, 3)
+        acc = np.zeros_like(full)
+        for lo, hi in zip(bounds[:-1], bounds[1:]):
+            acc += survey(h, g, kinds | tp.TRIPOLL_CLOSURE_HIST, window=(0, 0xFFFFFFFF), pivot_range=(int(lo), int(hi)))
+        assert np.array_equal(acc, full)
+    finally:
+        tp.tripoll_destroy(h)
 
 
 def _numpy_window_wedges(g, lo, hi):

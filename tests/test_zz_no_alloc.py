@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 def test_static_scratch_survey_equals_allocating_survey_twice():
     import torch
     g = synth.rmat_graph(13, 16, 11, ts_bits=20, num_vlabels=4, num_elabels=5)
-    kinds = tp.TRIPOLL_ALL_KINDS & ~tp.TRIPOLL_VERTEX_LOCAL
+    kinds = tp.TRIPOLL_ALL_KINDS & ~(tp.TRIPOLL_VERTEX_LOCAL | tp.TRIPOLL_EDGE_LOCAL)
     dev = [torch.from_numpy(a).cuda() for a in (g.src, g.dst, g.ts, g.elabel, g.vlabel)]
     h = tp.tripoll_graph_create(*dev, g.n, g.num_vlabels, g.num_elabels)
     try:
