@@ -673,8 +673,9 @@ struct __align__(16) WarpSmem {
     uint8_t vl[kWarpMaxQ];
 };
 
+// 5 resident blocks per SM, like the block kernel (the register cap that sets)
 template <int F>
-__global__ void __launch_bounds__(kBlockThreads) survey_warp_kernel(GraphDev g, const WorkItem* __restrict__ items,
+__global__ void __launch_bounds__(kBlockThreads, 5) survey_warp_kernel(GraphDev g, const WorkItem* __restrict__ items,
                                                                     uint32_t n_items, SurveyArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long* s_tab = reinterpret_cast<unsigned long long*>(smem);
