@@ -248,9 +248,7 @@ def run_tripoll(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "strong", "vs_baseline": None, "dtype": "u32/u64 integer", "data": "synthetic",
-        "config": {"workload": f"R-MAT scale {args.scale}, edge factor 16, a/b/c/d .57/.19/.19/.05, seed 1; "
-                               "ts uniform [0,2^30), vlabel 16, etype Zipf(1.2) over 8; survey = count + "
-                               "closure histogram + edge-type triples in window [2^28, 3*2^28-1]",
+        "config": {"workload": rmat_workload(args.scale),
                    "step": "build G+ from device-resident edge arrays + survey + release",
                    "input_edges": m_in, "edges": info["num_edges"], "wedges": info["wedges"], "wedge_checks_in_window": wedge_checks,
                    "triangles_in_window": triangles, "l2": "inputs larger than L2 (126 MB)",
@@ -288,6 +286,12 @@ def cpu_baseline(args, scale=None):
                       f"{tri} triangles in {dt:.2f} s"}
 
 
+def rmat_workload(scale):
+    return (f"R-MAT scale {scale}, edge factor 16, a/b/c/d .57/.19/.19/.05, seed 1; ts uniform [0,2^30), "
+            "vlabel 16, etype Zipf(1.2) over 8; survey = count + closure histogram + edge-type triples in window "
+            "[2^28, 3*2^28-1]")
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -309,9 +313,12 @@ def run_reference(args):
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": s * 1e3, "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "u32/u64 integer", "data": "synthetic",
-            "config": {"workload": f"R-MAT scale {args.cpu_scale} sample of the scale-24 recipe"},
+            "config": {"workload": rmat_workload(args.scale),
+                       "step": "the oracle on the host cores over a bounded sample of the workload",
+                       "parallelism": f"{cores} host threads"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"R-MAT scale {args.cpu_scale}, same recipe, per step"},
+                             "sample": f"each step: R-MAT scale {args.cpu_scale} with the same recipe (seed 1), "
+                                       f"full survey including the build, {tri} triangles"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
