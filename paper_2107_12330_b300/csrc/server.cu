@@ -5,10 +5,14 @@
 // order while fewer than max_inflight are on the device and their scratch
 // (the device accumulator of the result) fits under the budget; each admitted
 // request is launched on one of several CUDA streams, so requests of different
-// graphs, kinds and windows overlap on the GPU.  A host function enqueued
-// after the result copy marks the request done, returns its budget and wakes
-// the dispatcher, which admits whatever arrived meanwhile.  Results are the
-// same integer tables tripoll_survey computes for the request alone.
+// graphs, kinds and windows overlap on the GPU.  A request on a large graph
+// (kLargeEdges edges or more) already fills the GPU, and two of them at once
+// only evict each other's working sets from L2: large requests run one at a
+// time, and small ones behind a waiting large one are admitted past it.  A
+// host function enqueued after the result copy marks the request done,
+// returns its budget and wakes the dispatcher, which admits whatever arrived
+// meanwhile.  Results are the same integer tables tripoll_survey computes for
+// the request alone.
 #include <chrono>
 #include <cstring>
 #include <condition_variable>
@@ -24,6 +28,8 @@
 namespace tp {
 namespace {
 
+constexpr uint64_t kLargeEdges = 1ull << 25;  // graphs whose survey alone fills the GPU
+
 uint64_t now_ns() {
     return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
                std::chrono::steady_clock::now().time_since_epoch())
@@ -36,6 +42,7 @@ struct Request {
     uint64_t words = 0;
     uint64_t bytes = 0;          // device scratch charged to the budget
     bool view = false;           // survey through a window view of the graph
+    bool large = false;          // on a graph of kLargeEdges edges or more
     uint64_t* host = nullptr;    // pinned result buffer
     size_t host_cap = 0;
     uint64_t t_submit = 0, t_done = 0;
@@ -60,7 +67,7 @@ struct tripoll_server {
     std::unordered_map<uint64_t, tp::Request*> reqs;
     std::multimap<size_t, uint64_t*> pinned_pool;  // free pinned buffers by capacity
     uint64_t next_id = 1;
-    uint32_t inflight = 0;
+    uint32_t inflight = 0, large_inflight = 0;
     uint64_t in_use = 0;
     bool stop = false;
     std::thread dispatcher;
@@ -76,6 +83,7 @@ void CUDART_CB on_request_done(void* arg) {
     r->t_done = now_ns();
     r->done = true;
     s->inflight -= 1;
+    s->large_inflight -= r->large ? 1 : 0;
     s->in_use -= r->bytes;
     s->cv.notify_all();
 }
@@ -98,24 +106,37 @@ int launch_request(tripoll_server* s, Request* r, cudaStream_t st) {
     return TRIPOLL_OK;
 }
 
+// May r start now?  (lock held)
+bool admissible(const tripoll_server* s, const Request* r) {
+    if (r->large && s->large_inflight > 0) return false;
+    return s->in_use + r->bytes <= s->cap || s->inflight == 0;
+}
+
 void dispatcher_loop(tripoll_server* s) {
     cudaSetDevice(s->device);
     std::unique_lock<std::mutex> lk(s->mu);
     while (true) {
         s->cv.wait(lk, [&] {
             if (s->stop) return true;
-            if (s->pending.empty() || s->inflight >= s->max_inflight) return false;
-            Request* r = s->reqs[s->pending.front()];
-            return s->in_use + r->bytes <= s->cap || s->inflight == 0;
+            if (s->inflight >= s->max_inflight) return false;
+            for (uint64_t id : s->pending)
+                if (admissible(s, s->reqs[id])) return true;
+            return false;
         });
         if (s->stop) break;
-        // one admission round: everything that fits now, in arrival order
+        // one admission round: everything that may start now, in arrival order;
+        // requests that must wait keep their place in the queue
         std::vector<Request*> round;
-        while (!s->pending.empty() && s->inflight < s->max_inflight) {
-            Request* r = s->reqs[s->pending.front()];
-            if (s->in_use + r->bytes > s->cap && s->inflight > 0) break;
-            s->pending.pop_front();
+        for (auto it = s->pending.begin(); it != s->pending.end() && s->inflight < s->max_inflight;) {
+            Request* r = s->reqs[*it];
+            if (!admissible(s, r)) {
+                if (!r->large) break;  // over budget: keep arrival order
+                ++it;                  // a large request waits for the one running; smaller ones pass
+                continue;
+            }
+            it = s->pending.erase(it);
             s->inflight += 1;
+            s->large_inflight += r->large ? 1 : 0;
             s->in_use += r->bytes;
             round.push_back(r);
         }
@@ -133,6 +154,7 @@ void dispatcher_loop(tripoll_server* s) {
                 round[i]->t_done = now_ns();
                 round[i]->done = true;
                 s->inflight -= 1;
+                s->large_inflight -= round[i]->large ? 1 : 0;
                 s->in_use -= round[i]->bytes;
                 s->cv.notify_all();
             }
@@ -195,6 +217,7 @@ extern "C" int tripoll_server_submit(tripoll_server_t s, uint32_t slot, uint32_t
     r->t_hi = t_hi;
     r->words = make_layout(kind_mask, g->Lv, g->Le, g->n, g->m).words * g->num_graphs;
     r->bytes = r->words * 8 + 16;
+    r->large = g->m >= kLargeEdges;
     r->server = s;
     if (r->bytes > s->cap) {
         delete r;
