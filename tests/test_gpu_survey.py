@@ -61,7 +61,7 @@ def test_host_and_device_results_and_inputs_agree():
 
 def test_empty_and_degenerate_graphs():
     # no edges at all, only loops, a single repeated edge, isolated vertices
-    for src, dst, n in [([], [], 5), ([0, 1, 2], [0, 1, 2], 3), ([0, 0, 1, 1], [1, 1, 0, 0], 4),
+    for src, dst, n in [([], [], 0), ([], [], 5), ([0, 1, 2], [0, 1, 2], 3), ([0, 0, 1, 1], [1, 1, 0, 0], 4),
                         ([0, 1, 2], [1, 2, 0], 1000)]:
         src = np.array(src, np.uint32)
         dst = np.array(dst, np.uint32)
@@ -197,6 +197,13 @@ def test_batched_graphs_match_each_alone():
     for i, g in enumerate(graphs):
         want, _ = oracle_vector(g, kinds)
         assert_equal_tables(out[i * w:(i + 1) * w], want, kinds, g)
+
+
+def test_largest_label_counts():
+    """256 vertex and 256 edge labels: triple tables of 256^3 words, far past the on-chip record mirror."""
+    g = synth.tiny_random_graph(21, 400, 30000, ts_bits=10, num_vlabels=256, num_elabels=256)
+    check(g, ALL & ~(tp.TRIPOLL_VERTEX_LOCAL | tp.TRIPOLL_EDGE_LOCAL))
+    check(g, BASIC, window=(100, 700))
 
 
 def test_errors_are_reported_not_faulted():
