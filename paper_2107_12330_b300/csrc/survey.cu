@@ -13,16 +13,20 @@
 // (q,r) edge's plus vertex r's (from shared memory).
 //
 // Three kernels split the middle vertices by |Adj+(q)|: a warp-per-item kernel
-// for short out-lists (each warp its own table), a block-per-item kernel for
-// out-lists of up to kBlockChunk entries, and the same block kernel with
-// tables of kBigChunk entries for longer ones (longer still are cut into
-// chunks and each in-edge's segment is restricted to the chunk's value range
-// by binary search).  Inside an item the in-edges' segments form one flat index space of
-// units of 8 consecutive candidates that warps split evenly and walk 32 units at a
-// time: consecutive lanes read consecutive 32-byte units of the suffixes
-// (coalesced), and no lane idles however skewed the suffix lengths are.  Triangles outside the time window are pruned before any
-// probe where possible: in-edges (p,q) outside the window get empty segments
-// and entries (q,r) outside it are not inserted.
+// for out-lists of up to kWarpPlanQ entries (each warp its own table, staging
+// kWarpMaxQ entries of the window view at a time), a block-per-item kernel for
+// longer ones, staged kBlockChunk entries at a time, and the same block kernel
+// with kBigChunk-entry tables for the longest (a longer out-list is cut into
+// parts, and each in-edge's segment is restricted to the part's value range by
+// binary search).  Inside an item the in-edges' segments form one flat index
+// space of units of 8 consecutive candidates that warps split evenly and walk
+// 32 units at a time: consecutive lanes read consecutive 32-byte units of the
+// suffixes (coalesced), and no lane idles however skewed the suffix lengths
+// are.  Triangles outside the time window are pruned before any probe: a survey
+// with a window runs on a view of G+ holding only its in-window edges (the
+// window view below); without a view (the allocation-free survey) in-edges
+// (p,q) outside the window get empty segments and entries (q,r) outside it are
+// not inserted.
 //
 // Hits are queued per warp and folded 32 at a time, one per lane; the fold
 // aggregates inside the warp with __match_any_sync, then in shared memory,
@@ -200,7 +204,7 @@ struct QTable {
     uint32_t* deg;
     uint8_t* el;
     uint8_t* vl;
-    uint32_t size;  // slots: 3 per staged entry (load factor <= 1/3)
+    uint32_t size;  // slots in use (view_table_size)
 };
 
 #ifndef TP_TABLE_FACTOR
