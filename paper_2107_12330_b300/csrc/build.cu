@@ -17,8 +17,6 @@
 //              every middle vertex q the directed edges (p,q) that end at it
 //   stats      |E+|, |W+| = sum C(d+,2), d+ max, ...
 #include <cub/cub.cuh>
-#include <thrust/iterator/counting_iterator.h>
-#include <thrust/iterator/transform_iterator.h>
 
 #include <algorithm>
 #include <utility>
@@ -94,34 +92,14 @@ __global__ void canon_kernel(const uint32_t* __restrict__ src, const uint32_t* _
     }
 }
 
-// 1 at the first record of each run of equal keys (the sorted canonical pairs),
-// except the run of self-loops, whose sentinel key sorts last; 0 at i = m_in.
-struct RunHead {
-    const uint64_t* key;
-    uint64_t m_in;
-    uint64_t sentinel;
-    __host__ __device__ uint64_t operator()(uint64_t i) const {
-        return (i < m_in && key[i] != sentinel && (i == 0 || key[i] != key[i - 1])) ? 1u : 0u;
-    }
+struct MinOp {
+    __device__ __forceinline__ uint64_t operator()(uint64_t a, uint64_t b) const { return a < b ? a : b; }
 };
 
-// One unique edge per run of equal keys, at the run's rank among the runs: the
-// key, and the minimum payload (ts << 8 | elabel) of the run's records -- the
-// chronologically first record, edge label as the tie-break.  Runs are short
-// (duplicate records), so the thread at a run's head walks it.
-__global__ void dedup_runs_kernel(const uint64_t* __restrict__ key, const uint64_t* __restrict__ val, uint64_t m_in,
-                                  uint64_t sentinel, const uint64_t* __restrict__ rank, uint64_t* __restrict__ ukey,
-                                  uint64_t* __restrict__ uval) {
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m_in;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t k = key[i];
-        if (k == sentinel || (i > 0 && key[i - 1] == k)) continue;
-        uint64_t v = val[i];
-        for (uint64_t t = i + 1; t < m_in && key[t] == k; ++t) v = min(v, val[t]);
-        const uint64_t j = rank[i];
-        ukey[j] = k;
-        uval[j] = v;
-    }
+__global__ void unique_count_kernel(const uint64_t* ukey, const uint64_t* runs, uint64_t sentinel, uint64_t* m_out) {
+    uint64_t r = *runs;
+    if (r > 0 && ukey[r - 1] == sentinel) r -= 1;
+    *m_out = r;
 }
 
 // Degrees of the simple graph.  Keys are sorted, so the lanes of a warp mostly
@@ -445,24 +423,21 @@ int build_impl(const uint32_t* src_h, const uint32_t* dst_h, const uint32_t* ts_
         TP_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tb, kb, vb, m_in, 0, end_bit, s));
         TP_CUDA(tmp.alloc(tb, s));
         TP_CUDA(cub::DeviceRadixSort::SortPairs(tmp.ptr, tb, kb, vb, m_in, 0, end_bit, s));
-        // dedup into the buffers not holding the sorted data: the rank of each run
-        // by an exclusive scan of the run heads, then one write per run
+        // reduce-by-key into the buffers not holding the sorted data
         uint64_t* ukey = kb.Alternate();
         uint64_t* uval = vb.Alternate();
-        TP_CUDA(runs.alloc((m_in + 1) * 8, s));
-        auto heads = thrust::make_transform_iterator(thrust::counting_iterator<uint64_t>(0),
-                                                     RunHead{kb.Current(), m_in, sentinel});
+        TP_CUDA(runs.alloc(16, s));
         size_t tb2 = 0;
-        TP_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tb2, heads, runs.as<uint64_t>(), m_in + 1, s));
+        TP_CUDA(cub::DeviceReduce::ReduceByKey(nullptr, tb2, kb.Current(), ukey, vb.Current(), uval,
+                                               runs.as<uint64_t>(), MinOp(), m_in, s));
         if (tb2 > tb) TP_CUDA(tmp.alloc(tb2, s));
-        TP_CUDA(cub::DeviceScan::ExclusiveSum(tmp.ptr, tb2, heads, runs.as<uint64_t>(), m_in + 1, s));
-        if (m_in)
-            dedup_runs_kernel<<<grid_for(m_in), kThreads, 0, s>>>(kb.Current(), vb.Current(), m_in, sentinel,
-                                                                  runs.as<uint64_t>(), ukey, uval); ::tp::note_launch();
+        TP_CUDA(cub::DeviceReduce::ReduceByKey(tmp.ptr, tb2, kb.Current(), ukey, vb.Current(), uval,
+                                               runs.as<uint64_t>(), MinOp(), m_in, s));
+        if (m_in == 0) TP_CUDA(cudaMemsetAsync(runs.ptr, 0, 8, s));
+        unique_count_kernel<<<1, 1, 0, s>>>(ukey, runs.as<uint64_t>(), sentinel, runs.as<uint64_t>() + 1); ::tp::note_launch();
         TP_CUDA(cudaGetLastError());
-        TP_CUDA(cudaMemcpyAsync(&m, runs.as<uint64_t>() + m_in, 8, cudaMemcpyDeviceToHost, s));
+        TP_CUDA(cudaMemcpyAsync(&m, runs.as<uint64_t>() + 1, 8, cudaMemcpyDeviceToHost, s));
         TP_CUDA(cudaStreamSynchronize(s));
-        runs.release();
         if (m >= 0xFFFFFFFFull) return fail(TRIPOLL_ERR_INVALID_ARG, "more than 2^32-2 unique edges");
         // keep the buffers holding the unique arrays, drop the other two
         Scratch& kk = ukey == k0.as<uint64_t>() ? k0 : k1;
