@@ -3,6 +3,8 @@
 All survey arithmetic is integer, so every table must match exactly
 (no tolerance).  Inputs are seeded synthetic graphs from ``synth``.
 """
+import itertools
+
 import numpy as np
 import pytest
 
@@ -86,6 +88,38 @@ def test_complete_graph_long_out_lists():
     # a window: the chunks' value ranges come from their in-window entries only
     check(g, ALL & ~tp.TRIPOLL_VERTEX_LOCAL, window=(1 << 14, 3 << 14))
     check(g, tp.TRIPOLL_COUNT | tp.TRIPOLL_VERTEX_LOCAL | tp.TRIPOLL_EDGE_LOCAL, window=(0, 1 << 12))
+
+
+def test_out_lists_past_the_long_list_threshold():
+    """K_4200: every degree is 4199, so <+ is the id order and vertex i has 4199 - i out-edges; the first 103
+    vertices pass 4096 and are surveyed by the 2048-entry-table kernel, in parts.  Too many triangles for the
+    oracle (12.3 G), so the counts are checked against closed forms: C(n,3) triangles, all in bin 0 of the
+    closing-time histogram (equal timestamps), and vertex-label triples as products of binomials of the label
+    classes; a window that holds every edge gives the same tables."""
+    import math
+    n, sizes = 4200, [1400, 1500, 1300]
+    iu = np.triu_indices(n, 1)
+    src, dst = iu[0].astype(np.uint32), iu[1].astype(np.uint32)
+    ts = np.full(len(src), 77, np.uint32)
+    vl = np.repeat(np.arange(3), sizes).astype(np.uint8)
+    g = synth.Graph("K4200", n, src, dst, ts, vl, None, 3, 1, BASIC)
+    kinds = tp.TRIPOLL_COUNT | tp.TRIPOLL_CLOSURE_HIST | tp.TRIPOLL_VLABEL_TRIPLES
+    h = build(g)
+    try:
+        assert tp.tripoll_graph_stats(h)["dplus_max"] == n - 1
+        want = np.zeros(1 + 33 + 27, np.uint64)
+        want[0] = math.comb(n, 3)
+        want[1] = math.comb(n, 3)
+        for a, b, c in itertools.combinations_with_replacement(range(3), 3):
+            x = 1
+            for lab in set((a, b, c)):
+                x *= math.comb(sizes[lab], (a, b, c).count(lab))
+            want[34 + (a * 3 + b) * 3 + c] = x
+        for window in [(0, 0xFFFFFFFF), (77, 77)]:
+            got = survey(h, g, kinds, window=window)
+            assert np.array_equal(got, want), window
+    finally:
+        tp.tripoll_destroy(h)
 
 
 def test_edge_local_counts_view_in_place_and_shards():
