@@ -16,8 +16,10 @@ KINDS = [tp.TRIPOLL_COUNT, tp.TRIPOLL_CLOSURE_HIST, tp.TRIPOLL_VLABEL_TRIPLES, t
 
 
 def _graphs():
+    """Small graphs, and one (scale 22, about 64M edges) past the size from which the server runs requests one
+    at a time while small ones overlap them."""
     out = []
-    for i, sc in enumerate([10, 12, 14]):
+    for i, sc in enumerate([10, 12, 14, 22]):
         g = synth.rmat_graph(sc, 16, i + 1, ts_bits=24, num_vlabels=16, num_elabels=8)
         h = tp.tripoll_graph_create(g.src, g.dst, g.ts, g.elabel, g.vlabel, g.n, 16, 8)
         out.append((g, h))
