@@ -222,15 +222,20 @@ def test_batched_graphs_match_each_alone():
     nv = np.array([g.n for g in graphs], np.uint32)
     kinds = tp.TRIPOLL_COUNT | tp.TRIPOLL_CLOSURE_HIST | tp.TRIPOLL_VLABEL_TRIPLES
     h = tp.tripoll_batch_create(src, dst, ts, None, eoff, vl, nv, 4, 0)
+    window = (1 << 18, 3 << 18)  # the window view of a batched graph
     try:
         w = tp.tripoll_result_words(kinds, 4, 1, 0)
         out = np.zeros(w * len(graphs), np.uint64)
         tp.tripoll_survey(h, kinds, 0, 0xFFFFFFFF, out)
+        outw = np.zeros(w * len(graphs), np.uint64)
+        tp.tripoll_survey(h, kinds, window[0], window[1], outw)
     finally:
         tp.tripoll_destroy(h)
     for i, g in enumerate(graphs):
-        want, _ = oracle_vector(g, kinds)
+        want, _ = oracle_vector(g, kinds, window=(0, 0xFFFFFFFF))
         assert_equal_tables(out[i * w:(i + 1) * w], want, kinds, g)
+        want, _ = oracle_vector(g, kinds, window=window)
+        assert_equal_tables(outw[i * w:(i + 1) * w], want, kinds, g)
 
 
 def test_largest_label_counts():
