@@ -572,6 +572,13 @@ def run_serve(args):
     }
 
 
+def _ensure_built():
+    """Compile libtripoll.so (nvcc, sm_103a, in tree) if this checkout has none."""
+    from paper_2107_12330_b300 import build as libbuild
+    if not os.path.exists(libbuild.LIB):
+        libbuild.build()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -593,6 +600,8 @@ def main():
     ap.add_argument("--max-inflight", type=int, default=32)
     ap.add_argument("--load", type=float, default=0.7)
     args = ap.parse_args()
+    if args.impl != "reference":
+        _ensure_built()
     if args.impl == "reference":
         out = run_reference(args)
     elif args.workload == "batched":
