@@ -51,15 +51,40 @@ __device__ __forceinline__ uint32_t graph_of_edge(const uint64_t* eoff, uint32_t
     return lo;
 }
 
+// The records of a batch are grouped by graph, many to a graph.  Giving each block one contiguous
+// range of records lets a thread find the graph of its first record by binary search once and then
+// step forward over graph boundaries as its record index grows, instead of searching per record.
+__device__ __forceinline__ void block_records(uint64_t m, uint64_t& lo, uint64_t& hi) {
+    uint64_t per = (m + gridDim.x - 1) / gridDim.x;
+    per = (per + blockDim.x - 1) / blockDim.x * blockDim.x;  // warps stay aligned to 32 records
+    lo = min(m, (uint64_t)blockIdx.x * per);
+    hi = min(m, lo + per);
+}
+
+struct GraphCursor {
+    const uint64_t* eoff;  // G + 1 record offsets, eoff[G] = total records; null for one graph
+    uint32_t g;
+    __device__ GraphCursor(const uint64_t* e, uint32_t G, uint64_t i) : eoff(e), g(0) {
+        if (e && G) g = graph_of_edge(e, G, i);
+    }
+    // graph of record i, for non-decreasing i below eoff[G]
+    __device__ __forceinline__ uint32_t at(uint64_t i) {
+        while (eoff[g + 1] <= i) ++g;
+        return g;
+    }
+};
+
 __global__ void validate_edges_kernel(const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst,
                                       const uint8_t* __restrict__ el, uint64_t m, uint32_t n,
                                       const uint64_t* __restrict__ eoff, const uint32_t* __restrict__ nv,
                                       uint32_t G, uint32_t Le, unsigned* flags) {
     unsigned f = 0;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m;
-         i += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t lo, hi;
+    block_records(m, lo, hi);
+    GraphCursor gc(eoff, G, lo + threadIdx.x);
+    for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
         uint32_t lim = n;
-        if (eoff) lim = nv[graph_of_edge(eoff, G, i)];
+        if (eoff) lim = nv[gc.at(i)];
         if (src[i] >= lim || dst[i] >= lim) f |= 1u;
         if (el && el[i] >= Le) f |= 2u;
     }
@@ -78,11 +103,13 @@ __global__ void canon_kernel(const uint32_t* __restrict__ src, const uint32_t* _
                              const uint32_t* __restrict__ ts, const uint8_t* __restrict__ el, uint64_t m,
                              const uint64_t* __restrict__ eoff, const uint64_t* __restrict__ vbase, uint32_t G,
                              int b, uint64_t sentinel, uint64_t* __restrict__ key, uint64_t* __restrict__ val) {
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m;
-         i += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t lo, hi;
+    block_records(m, lo, hi);
+    GraphCursor gc(eoff, G, lo + threadIdx.x);
+    for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
         uint64_t u = src[i], v = dst[i];
         if (eoff) {
-            uint64_t base = vbase[graph_of_edge(eoff, G, i)];
+            uint64_t base = vbase[gc.at(i)];
             u += base;
             v += base;
         }
