@@ -21,3 +21,22 @@ def test_reference_arm_prints_one_json_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     assert "R-MAT scale 24" in d["config"]["workload"]
+
+
+def test_cpu_baseline_reports_all_cores_and_one_thread():
+    import argparse
+    sys.path.insert(0, ROOT)
+    import bench
+    d = bench.cpu_baseline(argparse.Namespace(cpu_scale=12))
+    assert d["kind"] == "oracle" and d["cores"] == (os.cpu_count() or 1) and d["value"] > 0
+    assert d["single_thread"]["cores"] == 1 and d["single_thread"]["value"] > 0
+    assert "scale 12" in d["sample"] and "scale 10" in d["single_thread"]["sample"]
+
+
+def test_compulsory_bytes_are_part_of_the_algorithmic_bytes():
+    sys.path.insert(0, ROOT)
+    import bench
+    st = {"num_vertices": 1000, "num_edges": 5000}
+    assert bench.compulsory_bytes(st) == 9 * 1000 + 26 * 5000
+    assert bench.algorithmic_bytes(st, 0, 0) == bench.compulsory_bytes(st)
+    assert bench.algorithmic_bytes(st, 7, 3) == bench.compulsory_bytes(st) + 4 * 7 + 5 * 3
