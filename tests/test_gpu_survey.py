@@ -3,6 +3,7 @@
 All survey arithmetic is integer, so every table must match exactly
 (no tolerance).  Inputs are seeded synthetic graphs from ``synth``.
 """
+import dataclasses
 import itertools
 
 import numpy as np
@@ -52,6 +53,21 @@ def test_tiny_graphs_all_kinds(seed, n, m):
 def test_windows(window):
     g = synth.tiny_random_graph(11, 300, 20000, ts_bits=6, num_vlabels=2, num_elabels=3)
     check(g, BASIC, window=window)
+
+
+@pytest.mark.parametrize("window", [(0, 0xFFFFFFFF), (0xFFFFFFFF, 0xFFFFFFFF), (1, 0xFFFFFFFE), (0, 0),
+                                    (0x80000000, 0xFFFFFFFF)])
+def test_full_range_timestamps(window):
+    """Timestamps over the whole uint32 range with 0 and 2^32-1 planted: closing times up to 2^32-1 fill the
+    last histogram bin (32), and windows start or end at the extreme timestamps."""
+    g = synth.tiny_random_graph(21, 120, 6000, ts_bits=32, num_vlabels=3, num_elabels=4)
+    ts = g.ts.copy()
+    ts[::7] = 0
+    ts[3::11] = 0xFFFFFFFF
+    g = dataclasses.replace(g, ts=ts)
+    got = check(g, ALL, window=window)
+    if window == (0, 0xFFFFFFFF):
+        assert got[1 + 32] > 0  # the count word, then bins 0..32
 
 
 def test_host_and_device_results_and_inputs_agree():
