@@ -415,10 +415,36 @@ __device__ __forceinline__ void fold_queue(const GraphDev& g, const SurveyArgs& 
     fold_warp<F>(keep, t, a, s_tab, grec, cnt, g.order);
 }
 
+// Fold the first 32 queued hits, all lanes active, and move the rest (nq - 32 < 32) to the front.
+template <int F, class PosT>
+__device__ __forceinline__ void fold_front(uint32_t& nq, const GraphDev& g, const SurveyArgs& a,
+                                           const QTable<PosT>& T, const InStage& S, const HitQueue& H,
+                                           const TriMeta& t, unsigned long long* s_tab, unsigned long long* grec,
+                                           unsigned long long& cnt) {
+    const uint32_t lane = threadIdx.x & 31;
+    __syncwarp();
+    fold_queue<F>(g, a, T, S, H, 0, 32, t, s_tab, grec, cnt);
+    const uint32_t left = nq - 32;
+    uint32_t mi = 0, mp = 0;
+    if (lane < left) {
+        mi = H.idx[32 + lane];
+        mp = H.pk[32 + lane];
+    }
+    __syncwarp();
+    if (lane < left) {
+        H.idx[lane] = mi;
+        H.pk[lane] = mp;
+    }
+    nq = left;
+    __syncwarp();
+}
+
 // Queue the hits of this lane's quad -- pos[i] >= 0 for a hit at CSR position
-// e0 + i of in-edge slot k -- one ballot per quad position, and fold 32 queued
-// hits, all lanes active, whenever 32 are waiting.  Called by the whole warp;
-// nq (< 32 on entry and exit) is warp-uniform.
+// e0 + i of in-edge slot k -- and fold 32 queued hits whenever 32 are waiting.
+// The warp's hits of a quad step enter the queue together (each lane writes its
+// own after those of the lanes below it) when they fit; otherwise, one quad
+// position at a time.  Called by the whole warp; nq (< 32 on entry and exit)
+// is warp-uniform.
 template <int F, class PosT>
 __device__ __forceinline__ void push_quad(const int (&pos)[4], uint32_t e0, uint32_t k, uint32_t& nq,
                                           const GraphDev& g, const SurveyArgs& a, const QTable<PosT>& T,
@@ -427,6 +453,29 @@ __device__ __forceinline__ void push_quad(const int (&pos)[4], uint32_t e0, uint
                                           unsigned long long& cnt) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
+    {
+        uint32_t total = 0, below = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const unsigned b = __ballot_sync(0xffffffffu, pos[i] >= 0);
+            total += __popc(b);
+            below += __popc(b & lt);
+        }
+        if (total == 0) return;
+        if (nq + total <= (uint32_t)kHitQ) {
+            uint32_t slot = nq + below;
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (pos[i] >= 0) {
+                    H.idx[slot] = e0 + i;
+                    H.pk[slot] = (uint32_t)pos[i] | (k << 16);
+                    ++slot;
+                }
+            nq += total;
+            while (nq >= 32) fold_front<F>(nq, g, a, T, S, H, t, s_tab, grec, cnt);
+            return;
+        }
+    }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const unsigned b = __ballot_sync(0xffffffffu, pos[i] >= 0);
@@ -437,24 +486,7 @@ __device__ __forceinline__ void push_quad(const int (&pos)[4], uint32_t e0, uint
             H.pk[slot] = (uint32_t)pos[i] | (k << 16);
         }
         nq += __popc(b);
-        if (nq >= 32) {
-            __syncwarp();
-            fold_queue<F>(g, a, T, S, H, 0, 32, t, s_tab, grec, cnt);
-            // move the (< 32) waiting entries to the front
-            const uint32_t left = nq - 32;
-            uint32_t mi = 0, mp = 0;
-            if (lane < left) {
-                mi = H.idx[32 + lane];
-                mp = H.pk[32 + lane];
-            }
-            __syncwarp();
-            if (lane < left) {
-                H.idx[lane] = mi;
-                H.pk[lane] = mp;
-            }
-            nq = left;
-            __syncwarp();
-        }
+        if (nq >= 32) fold_front<F>(nq, g, a, T, S, H, t, s_tab, grec, cnt);
     }
 }
 
