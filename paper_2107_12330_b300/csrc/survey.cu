@@ -29,9 +29,10 @@
 // not inserted.
 //
 // Hits are queued per warp and folded 32 at a time, one per lane; the fold
-// aggregates inside the warp with __match_any_sync, then in shared memory,
-// then with 64-bit global atomics once per block -- integer adds commute, so
-// the result is exact and schedule-independent.
+// aggregates inside the warp with __match_any_sync, then in 32-bit words of
+// shared memory, then with 64-bit global atomics when the words are moved out
+// (rarely, and once per block at its end) -- integer adds commute, so the
+// result is exact and schedule-independent.
 #include <cub/cub.cuh>
 #include <thrust/iterator/counting_iterator.h>
 #include <thrust/iterator/transform_iterator.h>
@@ -39,6 +40,7 @@
 #include <algorithm>
 #include <map>
 #include <mutex>
+#include <cstdlib>
 #include <tuple>
 
 #include "common.cuh"
@@ -69,7 +71,18 @@ namespace {
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 constexpr int kBlockThreads = 256;
 constexpr int kWarps = kBlockThreads / 32;
-constexpr uint32_t kSharedTableWords = 4096;  // on-chip mirror of the record prefix (32 KB)
+constexpr uint32_t kSharedTableWords = 4096;  // on-chip mirror of the record prefix (16 KB)
+// The mirror holds 32-bit partial sums: 32-bit shared-memory atomics cost less than 64-bit ones.
+// It is moved into the 64-bit record (each word exchanged with 0) often enough that no word
+// can reach 2^32.  A word gains at most one per hit, and an item has at most (staged entries)
+// x (in-edges) hits: 2^11 x 2^11 for block items, 2^7 x 2^6 for warp items.  So a block of a
+// block kernel moves it after every 2^9 items it takes (< 2^31 between moves), and each of the
+// 8 warps of a warp-kernel block after every 2^14 items it takes (< 8 x 2^27 = 2^30).  The
+// environment variable TRIPOLL_MIRROR_MOVE_LOG2 = k moves it every 2^k items instead when k is
+// smaller (tests use it to exercise the moves on small graphs).
+constexpr uint32_t kBlockMoveLog2 = 9, kWarpMoveLog2 = 14;
+static_assert(kBlockMoveLog2 + 11 + 11 < 32 && kWarpMoveLog2 + 7 + 6 + 3 < 32, "mirror words stay below 2^32");
+using MirrorWord = uint32_t;
 
 // feature bits of a kernel instantiation
 constexpr int F_TS = 1;     // timestamps (window or time kinds)
@@ -85,14 +98,27 @@ struct SurveyArgs {
     uint64_t p_lo, p_hi;      // pivot range
     uint32_t e_lo, e_hi;      // its CSR positions [off[p_lo], off[p_hi])
     bool restricted;          // pivot range is not all of [0, n)
+    // log2 of the items between moves of the shared mirror into the record: a block of a block
+    // kernel, a warp of the warp kernel.  (These sit in what would otherwise be padding: a larger
+    // argument block measurably slowed the survey kernels.)
+    uint8_t move_block_log2, move_warp_log2;
     Layout lay;
     unsigned long long* out;  // accumulator: one record, or num_graphs records (batched)
     uint32_t* counters;       // [3] item counters of the three kernels
 };
+static_assert(sizeof(SurveyArgs) == 128, "kernel argument block of the survey kernels");
 
 // Home slot of r in a table of `size` slots: a multiplicative hash scaled to size.
 __device__ __forceinline__ uint32_t hash_slot(uint32_t r, uint32_t size) {
     return __umulhi(r * 2654435761u, size);
+}
+
+// Move the shared mirror into the record, by one warp while the others keep adding to it.
+__device__ __forceinline__ void move_mirror_warp(MirrorWord* s_tab, uint32_t s_words, unsigned long long* out) {
+    for (uint32_t w = threadIdx.x & 31; w < s_words; w += 32) {
+        const MirrorWord v = atomicExch(&s_tab[w], 0u);
+        if (v) atomicAdd(&out[w], (unsigned long long)v);
+    }
 }
 
 // ceil(log2(d)) for d >= 2, and 0 for d in {0, 1}: the closing/opening-time bin (Alg. 4)
@@ -108,14 +134,14 @@ __device__ __forceinline__ void sort3(uint32_t& a, uint32_t& b, uint32_t& c) {
 }
 
 // Add `amount` to word `w` of the record: shared mirror when w < s_words, else global.
-__device__ __forceinline__ void rec_add(unsigned long long* s_tab, uint32_t s_words, unsigned long long* grec,
+__device__ __forceinline__ void rec_add(MirrorWord* s_tab, uint32_t s_words, unsigned long long* grec,
                                         uint64_t w, unsigned long long amount) {
-    if (w < s_words) atomicAdd(&s_tab[w], amount);
+    if (w < s_words) atomicAdd(&s_tab[w], (MirrorWord)amount);  // amount <= 32 here
     else atomicAdd(&grec[w], amount);
 }
 
 // Warp-aggregated increment of word `w` for the lanes in `mask` (the calling lanes).
-__device__ __forceinline__ void warp_add(unsigned mask, unsigned long long* s_tab, uint32_t s_words,
+__device__ __forceinline__ void warp_add(unsigned mask, MirrorWord* s_tab, uint32_t s_words,
                                          unsigned long long* grec, uint64_t w) {
     unsigned grp = __match_any_sync(mask, w);
     int leader = __ffs(grp) - 1;
@@ -134,7 +160,7 @@ struct TriMeta {
 
 // Fold the lanes with `keep` set (called by the whole warp).
 template <int F>
-__device__ __forceinline__ void fold_warp(bool keep, const TriMeta& t, const SurveyArgs& a, unsigned long long* s_tab,
+__device__ __forceinline__ void fold_warp(bool keep, const TriMeta& t, const SurveyArgs& a, MirrorWord* s_tab,
                                           unsigned long long* grec, unsigned long long& cnt,
                                           const uint32_t* __restrict__ order) {
     const unsigned km = __ballot_sync(0xffffffffu, keep);
@@ -383,7 +409,7 @@ struct HitQueue {
 template <int F, class PosT>
 __device__ __forceinline__ void fold_queue(const GraphDev& g, const SurveyArgs& a, const QTable<PosT>& T,
                                            const InStage& S, const HitQueue& H, uint32_t head, uint32_t nq, TriMeta t,
-                                           unsigned long long* s_tab, unsigned long long* grec,
+                                           MirrorWord* s_tab, unsigned long long* grec,
                                            unsigned long long& cnt) {
     const uint32_t lane = threadIdx.x & 31;
     bool keep = lane < nq;
@@ -419,7 +445,7 @@ __device__ __forceinline__ void fold_queue(const GraphDev& g, const SurveyArgs& 
 template <int F, class PosT>
 __device__ __forceinline__ void fold_front(uint32_t& nq, const GraphDev& g, const SurveyArgs& a,
                                            const QTable<PosT>& T, const InStage& S, const HitQueue& H,
-                                           const TriMeta& t, unsigned long long* s_tab, unsigned long long* grec,
+                                           const TriMeta& t, MirrorWord* s_tab, unsigned long long* grec,
                                            unsigned long long& cnt) {
     const uint32_t lane = threadIdx.x & 31;
     __syncwarp();
@@ -449,7 +475,7 @@ template <int F, class PosT>
 __device__ __forceinline__ void push_quad(const int (&pos)[4], uint32_t e0, uint32_t k, uint32_t& nq,
                                           const GraphDev& g, const SurveyArgs& a, const QTable<PosT>& T,
                                           const InStage& S, const HitQueue& H, const TriMeta& t,
-                                          unsigned long long* s_tab, unsigned long long* grec,
+                                          MirrorWord* s_tab, unsigned long long* grec,
                                           unsigned long long& cnt) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
@@ -501,7 +527,7 @@ template <int F, class PosT>
 __device__ __forceinline__ void scan_flat(const GraphDev& g, const SurveyArgs& a, const QTable<PosT>& T,
                                           const InStage& S, const HitQueue& H, uint32_t n_in, uint32_t f_begin,
                                           uint32_t f_end, uint32_t qbase, uint32_t q, uint32_t l_q, uint32_t d_q,
-                                          unsigned long long* s_tab, unsigned long long* grec,
+                                          MirrorWord* s_tab, unsigned long long* grec,
                                           unsigned long long& cnt) {
     const uint32_t lane = threadIdx.x & 31;
     TriMeta t = {};
@@ -576,15 +602,15 @@ __device__ __forceinline__ unsigned long long* record_of(const GraphDev& g, cons
     return g.graph_of ? a.out + (uint64_t)g.graph_of[q] * a.lay.words : a.out;
 }
 
-__device__ void flush_shared(unsigned long long* s_tab, uint32_t s_words, unsigned long long* out) {
+__device__ void flush_shared(MirrorWord* s_tab, uint32_t s_words, unsigned long long* out) {
     for (uint32_t w = threadIdx.x; w < s_words; w += blockDim.x)
-        if (s_tab[w]) atomicAdd(&out[w], s_tab[w]);
+        if (s_tab[w]) atomicAdd(&out[w], (unsigned long long)s_tab[w]);
 }
 
-__device__ void flush_count(unsigned long long cnt, const SurveyArgs& a, unsigned long long* s_tab,
+__device__ void flush_count(unsigned long long cnt, const SurveyArgs& a, MirrorWord* s_tab,
                             unsigned long long* grec) {
     for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-    if ((threadIdx.x & 31) == 0 && cnt && a.lay.o_count != ~0u) rec_add(s_tab, a.s_words, grec, a.lay.o_count, cnt);
+    if ((threadIdx.x & 31) == 0 && cnt && a.lay.o_count != ~0u) atomicAdd(&grec[a.lay.o_count], cnt);
 }
 
 // ---- block kernel: one item per block at a time ---------------------------------------------
@@ -611,8 +637,8 @@ __global__ void __launch_bounds__(kBlockThreads, CHUNK <= kBlockChunk ? 5 : 3)
     __shared__ typename BlockScan::TempStorage scan_tmp;
     __shared__ uint32_t s_item, s_total;
 
-    unsigned long long* s_tab = reinterpret_cast<unsigned long long*>(smem);
-    unsigned char* base = smem + ((a.s_words * 8 + 15) & ~15u);
+    MirrorWord* s_tab = reinterpret_cast<MirrorWord*>(smem);
+    unsigned char* base = smem + ((a.s_words * sizeof(MirrorWord) + 15) & ~15u);
     QTable<uint16_t> T;
     T.key = reinterpret_cast<uint32_t*>(base);
     T.ts = T.key + kBlockTable;
@@ -636,11 +662,14 @@ __global__ void __launch_bounds__(kBlockThreads, CHUNK <= kBlockChunk ? 5 : 3)
     for (uint32_t w = threadIdx.x; w < a.s_words; w += blockDim.x) s_tab[w] = 0;
     unsigned long long cnt = 0;
     unsigned long long* grec_prev = nullptr;
+    uint32_t taken = 0;  // items this block has taken (block-uniform)
 
     while (true) {
         if (threadIdx.x == 0) s_item = atomicAdd(&a.counters[CTR], 1u);
         __syncthreads();  // also: the previous item's table and stage are no longer read
         if (s_item >= n_items) break;
+        if ((++taken & ((1u << a.move_block_log2) - 1u)) == 0 && threadIdx.x < 32)
+            move_mirror_warp(s_tab, a.s_words, a.out);
         const uint32_t it = n_items - 1 - s_item;  // high positions first: the hubs' long items start early
         const WorkItem item = items[it];
         const uint32_t q = item.q;
@@ -714,8 +743,8 @@ template <int F>
 __global__ void __launch_bounds__(kBlockThreads, 5) survey_warp_kernel(GraphDev g, const WorkItem* __restrict__ items,
                                                                     uint32_t n_items, SurveyArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    unsigned long long* s_tab = reinterpret_cast<unsigned long long*>(smem);
-    WarpSmem* ws_all = reinterpret_cast<WarpSmem*>(smem + ((a.s_words * 8 + 15) & ~15u));
+    MirrorWord* s_tab = reinterpret_cast<MirrorWord*>(smem);
+    WarpSmem* ws_all = reinterpret_cast<WarpSmem*>(smem + ((a.s_words * sizeof(MirrorWord) + 15) & ~15u));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpSmem& ws = ws_all[warp];
     for (uint32_t w = threadIdx.x; w < a.s_words; w += blockDim.x) s_tab[w] = 0;
@@ -726,12 +755,14 @@ __global__ void __launch_bounds__(kBlockThreads, 5) survey_warp_kernel(GraphDev 
     S.j0 = ws.j0; S.jend = ws.jend; S.tpq = ws.tpq; S.meta = ws.meta; S.p = ws.p; S.e = ws.e; S.pp = ws.pp;
     unsigned long long cnt = 0;
     unsigned long long* grec_prev = nullptr;
+    uint32_t taken = 0;  // items this warp has taken (warp-uniform)
 
     while (true) {
         uint32_t it = 0;
         if (lane == 0) it = atomicAdd(&a.counters[0], 1u);
         it = __shfl_sync(0xffffffffu, it, 0);
         if (it >= n_items) break;
+        if ((++taken & ((1u << a.move_warp_log2) - 1u)) == 0) move_mirror_warp(s_tab, a.s_words, a.out);
         const WorkItem item = items[it];
         const uint32_t q = item.q;
         unsigned long long* grec = record_of(g, a, q);
@@ -888,7 +919,7 @@ int blocks_per_sm(const void* kernel, size_t smem) {
 template <int F>
 void launch_f(const tripoll_graph* g, const GraphDev& gd, const SurveyArgs& a, cudaStream_t s, int sms) {
     if (g->n_items_warp) {
-        size_t sm = ((a.s_words * 8 + 15) & ~15u) + kWarps * sizeof(WarpSmem);
+        size_t sm = ((a.s_words * sizeof(MirrorWord) + 15) & ~15u) + kWarps * sizeof(WarpSmem);
         const int per = blocks_per_sm((const void*)survey_warp_kernel<F>, sm);
         uint64_t blocks = (uint64_t)per * sms;
         blocks = std::min<uint64_t>(blocks, (g->n_items_warp + kWarps - 1) / kWarps);
@@ -896,14 +927,14 @@ void launch_f(const tripoll_graph* g, const GraphDev& gd, const SurveyArgs& a, c
                                                                          (uint32_t)g->n_items_warp, a); ::tp::note_launch();
     }
     if (g->n_items_block) {
-        size_t sm = ((a.s_words * 8 + 15) & ~15u) + block_smem_fixed<F, kBlockChunk>();
+        size_t sm = ((a.s_words * sizeof(MirrorWord) + 15) & ~15u) + block_smem_fixed<F, kBlockChunk>();
         const int per = blocks_per_sm((const void*)survey_block_kernel<F, kBlockChunk, 1>, sm);
         uint64_t blocks = std::min<uint64_t>((uint64_t)per * sms, g->n_items_block);
         survey_block_kernel<F, kBlockChunk, 1><<<(unsigned)blocks, kBlockThreads, sm, s>>>(
             gd, g->items_block, (uint32_t)g->n_items_block, a); ::tp::note_launch();
     }
     if (g->n_items_big) {
-        size_t sm = ((a.s_words * 8 + 15) & ~15u) + block_smem_fixed<F, kBigChunk>();
+        size_t sm = ((a.s_words * sizeof(MirrorWord) + 15) & ~15u) + block_smem_fixed<F, kBigChunk>();
         const int per = blocks_per_sm((const void*)survey_block_kernel<F, kBigChunk, 2>, sm);
         uint64_t blocks = std::min<uint64_t>((uint64_t)per * sms, g->n_items_big);
         survey_block_kernel<F, kBigChunk, 2><<<(unsigned)blocks, kBlockThreads, sm, s>>>(
@@ -1035,6 +1066,19 @@ int launch_survey(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_
     if (sw == ~0ull) sw = lay.words;
     if (g->graph_of) sw = 0;
     a.s_words = (uint32_t)std::min<uint64_t>(sw, kSharedTableWords);
+    {
+        unsigned long kb = kBlockMoveLog2, kw = kWarpMoveLog2;
+        if (const char* e = std::getenv("TRIPOLL_MIRROR_MOVE_LOG2")) {
+            char* end = nullptr;
+            const unsigned long v = std::strtoul(e, &end, 10);
+            if (end != e) {
+                kb = std::min(v, kb);
+                kw = std::min(v, kw);
+            }
+        }
+        a.move_block_log2 = (uint8_t)kb;
+        a.move_warp_log2 = (uint8_t)kw;
+    }
     const bool window = !(t_lo == 0 && t_hi == 0xFFFFFFFFu);
     int F = 0;
     if (window || (kinds & (TRIPOLL_CLOSURE_HIST | TRIPOLL_OPEN_CLOSE_HIST))) F |= F_TS;

@@ -70,6 +70,18 @@ def test_full_range_timestamps(window):
         assert got[1 + 32] > 0  # the count word, then bins 0..32
 
 
+@pytest.mark.parametrize("log2", ["0", "4"])
+def test_shared_mirror_moves_leave_results_unchanged(log2, monkeypatch):
+    """A block sums into a 32-bit shared-memory mirror of the result record; to keep it below 2^32, a warp
+    moves it into the 64-bit record (exchanging each word with 0) every 2^k work items its block (or, in the
+    warp kernel, the warp) takes.  With k forced to 0 or 4 the moves happen thousands of times while other
+    warps keep adding; the result must still equal the oracle's."""
+    monkeypatch.setenv("TRIPOLL_MIRROR_MOVE_LOG2", log2)
+    g = synth.rmat_graph(14, 16, 5, ts_bits=24, num_vlabels=4, num_elabels=5)
+    check(g, ALL)
+    check(g, BASIC, window=(1 << 22, 3 << 22))
+
+
 def test_host_and_device_results_and_inputs_agree():
     g = synth.rmat_graph(11, 16, 3, ts_bits=20, num_vlabels=4, num_elabels=8)
     a = check(g, BASIC, host_result=True)
