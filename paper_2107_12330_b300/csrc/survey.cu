@@ -140,9 +140,15 @@ __device__ __forceinline__ void rec_add(MirrorWord* s_tab, uint32_t s_words, uns
     else atomicAdd(&grec[w], amount);
 }
 
-// Warp-aggregated increment of word `w` for the lanes in `mask` (the calling lanes).
+// Increment of word `w` by each lane in `mask` (the calling lanes).  When all of their words are
+// in the shared mirror, plain 32-bit shared atomics (the hardware resolves equal addresses) cost
+// less than merging equal words first; words in global memory are merged within the warp.
 __device__ __forceinline__ void warp_add(unsigned mask, MirrorWord* s_tab, uint32_t s_words,
                                          unsigned long long* grec, uint64_t w) {
+    if (__all_sync(mask, w < s_words)) {
+        atomicAdd(&s_tab[w], 1u);
+        return;
+    }
     unsigned grp = __match_any_sync(mask, w);
     int leader = __ffs(grp) - 1;
     if ((int)(threadIdx.x & 31) == leader) rec_add(s_tab, s_words, grec, w, (unsigned long long)__popc(grp));
