@@ -102,7 +102,7 @@ class ClockSampler:
 # survey_block_kernel (profiles/survey_block_kernel_rmat22_ncu.md: 16.93 GB read
 # for 17.18 GB algorithmic at scale 22), valid only for the survey source it was
 # taken on (first 16 hex digits of its SHA-256); any other source reports null.
-PROFILED_SURVEY = {"sha256_16": "6c23a496f75dc446", "dram_per_alg_byte": (12.58364e9 + 3.299072e6) / 9.917552541e9,
+PROFILED_SURVEY = {"sha256_16": "ce7838f625d9e35f", "dram_per_alg_byte": (12.586697e9 + 3.769856e6) / 9.917552541e9,
                    "capture": "ncu, survey_block_kernel, R-MAT scale 22, scaled by algorithmic bytes"}
 
 
