@@ -23,6 +23,12 @@
  *     schedule.
  *   - Vertex ids are uint32 in [0, num_vertices); timestamps are uint32;
  *     labels are uint8 in [0, L).
+ *   - Environment: TRIPOLL_MIRROR_MOVE_LOG2 = k (0 <= k, read at each survey
+ *     call) makes the survey kernels move their on-chip partial sums into the
+ *     result after every 2^k work items instead of every 2^9 (block kernels)
+ *     or 2^14 (warp kernel) -- slower, same result; it exists so that tests
+ *     can exercise those moves on small graphs.  Values above the defaults
+ *     are ignored.
  */
 #ifndef TRIPOLL_H
 #define TRIPOLL_H

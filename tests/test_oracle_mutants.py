@@ -69,6 +69,12 @@ MUTANTS = [
     # per-edge participation credits (p,r) to (p,q)
     ("elocal_wrong_edge", "o->elocal[e_pr] += 1;", "o->elocal[e_pq] += 1;"),
     # per-thread vertex tables merged short by one
+    ("vtri_index_transposed", "o->vtri[((uint64_t)a * w->Lv + b) * w->Lv + c] += 1;",
+     "o->vtri[((uint64_t)a * w->Lv + c) * w->Lv + b] += 1;"),
+    ("etri_index_transposed", "o->etri[((uint64_t)a * w->Le + b) * w->Le + c] += 1;",
+     "o->etri[((uint64_t)c * w->Le + b) * w->Le + a] += 1;"),
+    ("degtri_index_transposed", "o->degtri[((uint64_t)a * HIST_BINS + b) * HIST_BINS + c] += 1;",
+     "o->degtri[((uint64_t)b * HIST_BINS + a) * HIST_BINS + c] += 1;"),
     ("merge_vlocal_short", "add_into(out->vlocal, o->vlocal, n);", "add_into(out->vlocal, o->vlocal, n ? n - 1 : 0);"),
 ]
 
