@@ -248,10 +248,10 @@ __device__ __forceinline__ uint32_t table_size(uint32_t len) { return max(kTable
 
 // Slots used for len staged entries out of cap: a window view stages only
 // in-window entries, so its tables use the room left by the out-of-window
-// ones: four times the slots per entry (load factor <= 1/12) while they fit,
+// ones: six times the slots per entry (load factor <= 1/18) while they fit,
 // which makes a probe that finds its home slot taken by another key rare.
 __device__ __forceinline__ uint32_t view_table_size(uint32_t len, bool view, uint32_t cap) {
-    return view ? min(table_size(4 * len), cap) : table_size(len);
+    return view ? min(table_size(6 * len), cap) : table_size(len);
 }
 
 // Insert the entries [i0, len) step `stride` of the staged out-list part at
