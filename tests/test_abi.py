@@ -3,6 +3,7 @@ declares; host-only helpers behave as documented (no GPU needed)."""
 import os
 import re
 
+import numpy as np
 import pytest
 
 import paper_2107_12330_b300 as tp
@@ -55,3 +56,18 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(tp, "_lib", None)
     with pytest.raises(OSError):
         tp.load_library(str(tmp_path / "libtripoll.so"))
+
+
+def test_split_result_matches_the_library_layout_for_every_kind_mask():
+    """The binding's table layout and the library's record size agree for all 2^9 kind masks: the parts
+    split_result cuts out are contiguous, in the header's order, and end exactly at tripoll_result_words."""
+    for Lv, Le, n, m in [(1, 1, 0, 0), (2, 3, 5, 7), (16, 8, 1000, 4000), (64, 16, 3, 2)]:
+        for mask in range(1, tp.TRIPOLL_ALL_KINDS + 1):
+            words = tp.tripoll_result_words(mask, Lv, Le, n, m)
+            vec = np.arange(words, dtype=np.uint64)
+            parts = tp.split_result(vec, mask, Lv, Le, n, m)
+            assert sum(len(p) for p in parts.values()) == words, (mask, Lv, Le)
+            o = 0
+            for p in parts.values():
+                assert len(p) == 0 or int(p[0]) == o
+                o += len(p)
