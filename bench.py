@@ -197,7 +197,7 @@ def run_tripoll(args):
     triangles = int(res0[0])
 
     clocks = ClockSampler(local)
-    launches0 = lib.tripoll_launch_count()
+    launches0 = tp.tripoll_launch_count()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if world > 1:
@@ -212,7 +212,7 @@ def run_tripoll(args):
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    launches = lib.tripoll_launch_count() - launches0
+    launches = tp.tripoll_launch_count() - launches0
     ms = start.elapsed_time(end) / args.steps
     survey_ms = [a.elapsed_time(b) for a, b in evs]
     survey_avg = sum(survey_ms) / len(survey_ms)
@@ -394,14 +394,14 @@ def run_batched(args):
     torch.cuda.synchronize()
     clocks = ClockSampler(0)
     clocks.start()
-    l0 = lib.tripoll_launch_count()
+    l0 = tp.tripoll_launch_count()
     start.record(stream)
     for k in range(args.steps):
         step(evs[k])
     end.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    launches = lib.tripoll_launch_count() - l0
+    launches = tp.tripoll_launch_count() - l0
     ms = start.elapsed_time(end) / args.steps
     survey_ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
     res = result.cpu().numpy().view(np.uint64).reshape(G, w)

@@ -182,6 +182,11 @@ def tripoll_batch_create(src, dst, ts, elabel, edge_offsets, vlabel, num_vertice
     return out.value
 
 
+def tripoll_launch_count():
+    """Kernels this library has launched in the process so far (host-side counter)."""
+    return int(load_library().tripoll_launch_count())
+
+
 def tripoll_result_words(kind_mask, num_vlabels, num_elabels, num_vertices=0, num_edges=0):
     return int(load_library().tripoll_result_words(kind_mask, num_vlabels, num_elabels, num_vertices, num_edges))
 

@@ -25,6 +25,9 @@ def test_library_exports_every_declared_symbol():
     missing = [n for n in names if not hasattr(lib, n)]
     assert not missing, missing
     assert set(names) <= set(tp.EXPORTS)
+    # the Python binding carries the same names as the C entry points
+    unbound = [n for n in names if not callable(getattr(tp, n, None))]
+    assert not unbound, unbound
 
 
 def test_result_words_layout():
