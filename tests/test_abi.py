@@ -74,3 +74,36 @@ def test_split_result_matches_the_library_layout_for_every_kind_mask():
             for p in parts.values():
                 assert len(p) == 0 or int(p[0]) == o
                 o += len(p)
+
+
+def test_invalid_arguments_are_rejected_before_any_gpu_work():
+    """Argument checks of the C ABI run on the host before the library touches the device, so on any machine
+    each bad call returns TRIPOLL_ERR_INVALID_ARG with a message, and nothing is built or launched."""
+    src = np.array([0, 1], np.uint32)
+    dst = np.array([1, 2], np.uint32)
+    ts = np.array([1, 2], np.uint32)
+    el = np.array([0, 1], np.uint8)
+    z = np.zeros(1, np.uint64)
+    cases = {
+        "no vertex label classes": lambda: tp.tripoll_graph_create(src, dst, ts, None, None, 3, 0, 1),
+        "257 vertex label classes": lambda: tp.tripoll_graph_create(src, dst, ts, None, None, 3, 257, 1),
+        "edge labels without classes": lambda: tp.tripoll_graph_create(src, dst, ts, el, None, 3, 1, 0),
+        "257 edge label classes": lambda: tp.tripoll_graph_create(src, dst, ts, el, None, 3, 1, 257),
+        "batch offsets not from 0": lambda: tp.tripoll_batch_create(
+            src, dst, ts, None, np.array([1, 2], np.uint64), None, np.array([3], np.uint32), 1, 1),
+        "batch offsets decreasing": lambda: tp.tripoll_batch_create(
+            np.r_[src, src], np.r_[dst, dst], np.r_[ts, ts], None, np.array([0, 3, 2], np.uint64), None,
+            np.array([3, 3], np.uint32), 1, 1),
+        "survey of no graph": lambda: tp.tripoll_survey(None, tp.TRIPOLL_COUNT, 0, 1, z),
+        "pivot range of no graph": lambda: tp.tripoll_survey_range(None, tp.TRIPOLL_COUNT, 0, 1, 0, 1, z),
+        "static survey of no graph": lambda: tp.tripoll_survey_static(None, tp.TRIPOLL_COUNT, 0, 1, z),
+        "wedge checks of no graph": lambda: tp.tripoll_wedge_checks(None),
+        "statistics of no graph": lambda: tp.tripoll_graph_stats(None),
+        "partition of no graph": lambda: tp.tripoll_partition_pivots(None, 2),
+        "server without budget": lambda: tp.tripoll_server_create(0, 4),
+        "server without requests in flight": lambda: tp.tripoll_server_create(1 << 20, 0),
+    }
+    for what, call in cases.items():
+        with pytest.raises(tp.TripollError) as e:
+            call()
+        assert e.value.status == tp.TRIPOLL_ERR_INVALID_ARG, what
