@@ -284,6 +284,18 @@ def run_tripoll(args):
     return out
 
 
+def cpu_model() -> str:
+    """The host CPU's model name, as the kernel reports it (empty when unknown)."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return ""
+
+
 def cpu_baseline(args, scale=None):
     """The oracle as it stands on the host cores, over a bounded sample: the same
     R-MAT recipe at a smaller scale (the full scale-24 survey takes the oracle
@@ -303,7 +315,7 @@ def cpu_baseline(args, scale=None):
     r1 = oracle.survey_graph(g1, threads=1, extras=())
     dt1 = time.perf_counter() - t0
     tri1 = int(r1["count"][0])
-    return {"value": tri / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+    return {"value": tri / dt, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
             "sample": f"R-MAT scale {scale} with the same recipe (seed 1), full survey incl. build, "
                       f"{tri} triangles in {dt:.2f} s",
             "single_thread": {"value": tri1 / dt1, "unit": UNIT, "cores": 1,
@@ -340,7 +352,7 @@ def run_reference(args):
             "config": {"workload": rmat_workload(args.scale),
                        "step": "the oracle on the host cores over a bounded sample of the workload",
                        "parallelism": f"{cores} host threads"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
                              "sample": f"each step: R-MAT scale {args.cpu_scale} with the same recipe (seed 1), "
                                        f"full survey including the build, {tri} triangles"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

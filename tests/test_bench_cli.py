@@ -31,6 +31,7 @@ def test_cpu_baseline_reports_all_cores_and_one_thread():
     assert d["kind"] == "oracle" and d["cores"] == (os.cpu_count() or 1) and d["value"] > 0
     assert d["single_thread"]["cores"] == 1 and d["single_thread"]["value"] > 0
     assert "scale 12" in d["sample"] and "scale 10" in d["single_thread"]["sample"]
+    assert isinstance(d["cpu_model"], str)
 
 
 def test_compulsory_bytes_are_part_of_the_algorithmic_bytes():
