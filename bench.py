@@ -216,10 +216,11 @@ def run_tripoll(args):
     ms = start.elapsed_time(end) / args.steps
     survey_ms = [a.elapsed_time(b) for a, b in evs]
     survey_avg = sum(survey_ms) / len(survey_ms)
-    t = torch.tensor([ms, survey_avg], dtype=torch.float64, device=dev)
+    survey_med = float(np.median(survey_ms))
+    t = torch.tensor([ms, survey_avg, survey_med], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms, survey_avg = float(t[0]), float(t[1])
+    ms, survey_avg, survey_med = float(t[0]), float(t[1]), float(t[2])
     res1 = result.cpu().numpy().view(np.uint64)
     assert np.array_equal(res0, res1), "survey result changed between steps"
 
@@ -267,7 +268,7 @@ def run_tripoll(args):
                    "input_edges": m_in, "edges": info["num_edges"], "wedges": info["wedges"], "wedge_checks_in_window": wedge_checks,
                    "triangles_in_window": triangles, "l2": "inputs larger than L2 (126 MB)",
                    "parallelism": f"pivot shards x{world}"},
-        "survey_ms": survey_avg, "build_ms": ms - survey_avg,
+        "survey_ms": survey_avg, "survey_ms_median": survey_med, "build_ms": ms - survey_avg,
         "survey_triangles_per_s": triangles / (survey_avg * 1e-3),
         "wedge_checks_per_s": wedge_checks / (survey_avg * 1e-3),
         "roofline": {"bound": "hbm", "kernel": "survey (wedge-check + fold kernels, one launch pair)",
