@@ -99,9 +99,9 @@ class ClockSampler:
 
 
 # DRAM traffic of the survey per algorithmic byte, from the last ncu capture of
-# survey_block_kernel (profiles/survey_block_kernel_rmat22_ncu.md: 16.93 GB read
-# for 17.18 GB algorithmic at scale 22), valid only for the survey source it was
-# taken on (first 16 hex digits of its SHA-256); any other source reports null.
+# survey_block_kernel on R-MAT scale 22 (12.59 GB read, 3.6 MB written, for 9.92 GB
+# of algorithmic bytes), valid only for the survey source it was taken on (first 16
+# hex digits of its SHA-256); any other source reports null.
 PROFILED_SURVEY = {"sha256_16": "143bde6d9ad0d226", "dram_per_alg_byte": (12.586617e9 + 3.648512e6) / 9.917552541e9,
                    "capture": "ncu, survey_block_kernel, R-MAT scale 22, scaled by algorithmic bytes"}
 
@@ -131,6 +131,16 @@ def algorithmic_bytes(st: dict, wedge_checks: int, triangles_in_window: int) -> 
     per triangle in the window."""
     n, m = st["num_vertices"], st["num_edges"]
     return 9 * n + (10 + 16) * m + 4 * wedge_checks + 5 * triangles_in_window
+
+
+def merge_path_bytes(st: dict, triangles_in_window: int) -> int:
+    """The bytes a merge-path survey would move: offsets, pivot label and the
+    augmented out-list of every pivot once (9 B per vertex, 9 B per edge), the whole out-list of q once per
+    directed edge (p,q) (4 B per entry: sum over (p,q) of d+(q)) plus q's label, and 6 B per triangle.  This
+    library never re-reads Adj+(q) per in-edge -- it stages it once on chip and probes it with the pivots'
+    suffixes -- so this figure counts reads it does not make; it is reported beside the method's own bytes."""
+    n, m = st["num_vertices"], st["num_edges"]
+    return 9 * n + 9 * m + 4 * st["q_list_words"] + m + 6 * triangles_in_window
 
 
 def compulsory_bytes(st: dict) -> int:
@@ -177,15 +187,18 @@ def run_tripoll(args):
     bounds = tp.tripoll_partition_pivots(h0, world)
     tp.tripoll_destroy(h0)
 
+    phases = []
+
     def step(ev=None):
         h = build()
 
         def survey_range(lo, hi, out):
             if ev is not None:
                 ev[0].record(stream)
-            tp.tripoll_survey_range(h, kinds, t_lo, t_hi, lo, hi, out, stream=stream)
-            if ev is not None:
+                phases.append(tp.tripoll_survey_timed(h, kinds, t_lo, t_hi, lo, hi, out, stream=stream))
                 ev[1].record(stream)
+            else:
+                tp.tripoll_survey_range(h, kinds, t_lo, t_hi, lo, hi, out, stream=stream)
 
         sharded_survey(survey_range, bounds, rank, result, dist.all_reduce if world > 1 else (lambda x: None))
         tp.tripoll_destroy(h)
@@ -216,11 +229,14 @@ def run_tripoll(args):
     ms = start.elapsed_time(end) / args.steps
     survey_ms = [a.elapsed_time(b) for a, b in evs]
     survey_avg = sum(survey_ms) / len(survey_ms)
-    survey_med = float(np.median(survey_ms))
-    t = torch.tensor([ms, survey_avg, survey_med], dtype=torch.float64, device=dev)
+    survey_med = float(np.percentile(survey_ms, 50))
+    survey_p99 = float(np.percentile(survey_ms, 99))
+    ph = np.mean(np.array(phases), axis=0) if phases else np.zeros(4)
+    t = torch.tensor([ms, survey_avg, survey_med, survey_p99] + list(ph), dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms, survey_avg, survey_med = float(t[0]), float(t[1]), float(t[2])
+    ms, survey_avg, survey_med, survey_p99 = float(t[0]), float(t[1]), float(t[2]), float(t[3])
+    ph = [float(x) for x in t[4:8]]
     res1 = result.cpu().numpy().view(np.uint64)
     assert np.array_equal(res0, res1), "survey result changed between steps"
 
@@ -254,11 +270,16 @@ def run_tripoll(args):
         if world > 1:
             dist.destroy_process_group()
         return None
+    meta_cost = metadata_cost(tp, build, stream) if world == 1 and args.metadata_cost else None
     peak, peak_kind = _peaks()
     alg = algorithmic_bytes(info, wedge_checks, triangles)
     achieved = alg / (survey_avg * 1e-3) / 1e9
+    merge_bytes = merge_path_bytes(info, triangles)
     traffic, traffic_src = survey_traffic(alg)
     value = triangles / (ms * 1e-3)
+    l2_note = ("inputs larger than L2 (126 MB): %.2f GB of edge records, %.2f GB of graph"
+               % (m_in * 13 / 1e9, info["device_bytes"] / 1e9)) if info["device_bytes"] > 126e6 else \
+        "graph smaller than L2 (126 MB); the edge records are rebuilt into it every step"
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -266,16 +287,27 @@ def run_tripoll(args):
         "config": {"workload": rmat_workload(args.scale),
                    "step": "build G+ from device-resident edge arrays + survey + release",
                    "input_edges": m_in, "edges": info["num_edges"], "wedges": info["wedges"], "wedge_checks_in_window": wedge_checks,
-                   "triangles_in_window": triangles, "l2": "inputs larger than L2 (126 MB)",
+                   "triangles_in_window": triangles, "l2": l2_note,
                    "parallelism": f"pivot shards x{world}"},
-        "survey_ms": survey_avg, "survey_ms_median": survey_med, "build_ms": ms - survey_avg,
+        "survey_ms": survey_avg, "survey_ms_p50": survey_med, "survey_ms_p99": survey_p99,
+        "survey_latency": {"p50_ms": survey_med, "p99_ms": survey_p99, "over": f"{args.steps} timed surveys"},
+        "survey_phases_ms": {"window_view": ph[0], "survey_warp_kernel": ph[1], "survey_block_kernel": ph[2],
+                             "survey_block_kernel_long_lists": ph[3]},
+        "build_ms": ms - survey_avg,
         "survey_triangles_per_s": triangles / (survey_avg * 1e-3),
         "wedge_checks_per_s": wedge_checks / (survey_avg * 1e-3),
-        "roofline": {"bound": "hbm", "kernel": "survey (wedge-check + fold kernels, one launch pair)",
+        "roofline": {"bound": "hbm",
+                     "kernel": "survey launch group on one stream (window view, warp-item kernel, block-item "
+                               "kernel, long-list kernel); survey_block_kernel dominates (survey_phases_ms)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_source": peak_kind, "algorithmic_bytes": alg,
+                     "algorithmic_bytes_formula": "9n + 26m + 4 wedge checks of the window subgraph "
+                                                  "+ 5 per triangle in the window",
+                     "merge_path_bytes": merge_bytes,
+                     "merge_path_frac": merge_bytes / (survey_avg * 1e-3) / 1e9 / peak,
                      "compulsory_bytes": compulsory_bytes(info), "traffic": traffic,
                      "traffic_source": traffic_src},
+        "metadata_cost": meta_cost,
         "clocks": clk, "gpu_launches": int(launches), "e2e": e2e,
     }
     if world == 1 and not args.no_cpu_baseline:
@@ -283,6 +315,40 @@ def run_tripoll(args):
     if world > 1:
         dist.destroy_process_group()
     return out
+
+
+def metadata_cost(tp, build, stream):
+    """The cost of metadata in the survey (the paper's Sec. 5.10 measures a degree-triple callback against
+    the plain count and finds just under 2x): device time of the full-window survey with the count alone,
+    with the count and the degree-log triples, and with the count, closing-time histogram and vertex- and
+    edge-label triples, on the same graph (median of 3 after one warm-up each)."""
+    import torch
+    h = build()
+    try:
+        st = tp.tripoll_graph_stats(h)
+        out = {}
+        for name, kinds in (("count", tp.TRIPOLL_COUNT),
+                            ("count_degree_triples", tp.TRIPOLL_COUNT | tp.TRIPOLL_DEGREE_TRIPLES),
+                            ("count_hist_label_triples", tp.TRIPOLL_COUNT | tp.TRIPOLL_CLOSURE_HIST |
+                             tp.TRIPOLL_VLABEL_TRIPLES | tp.TRIPOLL_ELABEL_TRIPLES)):
+            w = tp.tripoll_result_words(kinds, st["num_vlabels"], max(1, st["num_elabels"]), st["num_vertices"])
+            res = torch.zeros(w, dtype=torch.int64, device="cuda")
+            times = []
+            for k in range(4):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                tp.tripoll_survey(h, kinds, 0, 0xFFFFFFFF, res, stream=stream)
+                b.record(stream)
+                torch.cuda.synchronize()
+                if k:
+                    times.append(a.elapsed_time(b))
+            out[name + "_ms"] = float(np.median(times))
+        out["degree_triples_over_count"] = out["count_degree_triples_ms"] / out["count_ms"]
+        out["label_tables_over_count"] = out["count_hist_label_triples_ms"] / out["count_ms"]
+        out["window"] = "full (every triangle)"
+        return out
+    finally:
+        tp.tripoll_destroy(h)
 
 
 def cpu_model() -> str:
@@ -545,8 +611,8 @@ def run_serve(args):
     for i in range(R):
         gi = (draws[4 * i] >> 32) * len(scales) >> 32
         kind = kinds_set[(draws[4 * i + 1] >> 32) * 4 >> 32]
-        lo = (draws[4 * i + 2] >> 40) % (1 << 24 + 1)
-        hi = (draws[4 * i + 3] >> 40) % (1 << 24 + 1)
+        lo = (draws[4 * i + 2] >> 40) % ((1 << 24) + 1)
+        hi = (draws[4 * i + 3] >> 40) % ((1 << 24) + 1)
         reqs.append((int(gi), kind, int(min(lo, hi)), int(max(lo, hi))))
     words = [tp.tripoll_result_words(k, 16, 8, infos[gi][0]) for gi, k, _, _ in reqs]
 
@@ -630,6 +696,7 @@ def main():
     ap.add_argument("--cpu-scale", type=int, default=19)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-metadata-cost", dest="metadata_cost", action="store_false")
     ap.add_argument("--graphs", type=int, default=20000)
     ap.add_argument("--plain-graphs", type=int, default=20000)
     ap.add_argument("--plain-build-graphs", type=int, default=200)

@@ -84,8 +84,11 @@ typedef enum {
  *                                    tripoll_graph_export); m = num_edges.
  *
  * A triangle is surveyed iff its three edge timestamps all lie in the inclusive
- * window [t_lo, t_hi]; [0, 0xFFFFFFFF] surveys every triangle.  This equals
- * surveying the subgraph of the edges whose timestamp lies in the window. */
+ * window [t_lo, t_hi]; [0, 0xFFFFFFFF] surveys every triangle.  The window
+ * selects triangles, not degrees: every table equals the survey of the
+ * subgraph of the edges whose timestamp lies in the window, except
+ * TRIPOLL_DEGREE_TRIPLES, whose d(v) stays the degree in the whole simple
+ * graph (the window leaves the order <+ of Sec. 3 unchanged too). */
 enum {
     TRIPOLL_COUNT = 1,
     TRIPOLL_CLOSURE_HIST = 2,
@@ -149,9 +152,11 @@ int tripoll_batch_create(const uint32_t* src, const uint32_t* dst, const uint32_
                          uint32_t num_vlabels, uint32_t num_elabels, void* cuda_stream,
                          tripoll_graph_t* out);
 
-/* Number of uint64 words of a result for kind_mask (TRIPOLL_VERTEX_LOCAL adds
- * num_vertices words, TRIPOLL_EDGE_LOCAL num_edges -- the unique edges of G+,
- * tripoll_graph_stats' num_edges --, the others fixed sizes listed above). */
+/* Number of uint64 words of a result for kind_mask: the sizes of the tables
+ * listed above (the folds of Alg. 2, 3, 4, Sec. 5.3 and Sec. 5.9), summed
+ * (TRIPOLL_VERTEX_LOCAL adds num_vertices words, TRIPOLL_EDGE_LOCAL num_edges
+ * -- the unique edges of G+, tripoll_graph_stats' num_edges).  Host-only; no
+ * error status (an unknown bit adds nothing). */
 uint64_t tripoll_result_words(uint32_t kind_mask, uint32_t num_vlabels, uint32_t num_elabels,
                               uint64_t num_vertices, uint64_t num_edges);
 
@@ -178,17 +183,31 @@ int tripoll_survey_range(tripoll_graph_t g, uint32_t kind_mask, uint32_t t_lo, u
                          uint64_t pivot_lo, uint64_t pivot_hi, uint64_t* result,
                          void* cuda_stream);
 
+/* tripoll_survey_range with the device time of each phase, for measurement:
+ * CUDA events recorded on cuda_stream around each phase give phase_ms[0]
+ * (building the window view), [1] (the kernel of middle vertices with short
+ * out-lists, one per warp), [2] (the block-per-item kernel) and [3] (the
+ * kernel of the longest out-lists), in milliseconds; a phase that does not run
+ * reads 0.  phase_ms: host, float[4].  The result is the same as
+ * tripoll_survey_range's.  Errors: those of tripoll_survey_range, INVALID_ARG
+ * for a NULL phase_ms.  Synchronises cuda_stream. */
+int tripoll_survey_timed(tripoll_graph_t g, uint32_t kind_mask, uint32_t t_lo, uint32_t t_hi,
+                         uint64_t pivot_lo, uint64_t pivot_hi, uint64_t* result, float* phase_ms,
+                         void* cuda_stream);
+
 /* tripoll_survey for callers that cannot allocate device memory where they
- * survey -- e.g. code whose stream is being captured into a CUDA graph, loops
- * that must never enter an allocator, or hosts whose device memory belongs to
+ * survey -- loops that must never enter an allocator (an allocation may block
+ * on the driver or on other streams), or hosts whose device memory belongs to
  * another framework.  The paper has no counterpart; this is a library
  * convenience.  Same arguments, kernels and result as tripoll_survey, but the
  * call allocates nothing: its scratch (the accumulation record and two work
  * counters) is a static 8 MiB device array that every GPU loading the library
  * holds until the process exits, and a window is applied in place (no window
  * view: out-of-window edges are skipped where they are met).
- *   - The first call on a device looks up that array's device address; make
- *     the first call before any stream capture on that device.
+ *   - The first call on a device looks up that array's device address (kept
+ *     for the life of the process, so the device's primary context must not
+ *     be reset while the library is loaded); make that first call before any
+ *     stream capture on the device.
  *   - Every call reuses the same array (each call clears the part it needs):
  *     calls whose GPU work overlaps -- on different streams, or from different
  *     threads -- race and corrupt each other's results.  Order them on one
@@ -207,7 +226,10 @@ int tripoll_survey_static(tripoll_graph_t g, uint32_t kind_mask, uint32_t t_lo, 
 int tripoll_partition_pivots(tripoll_graph_t g, uint32_t parts, uint64_t* bounds,
                              void* cuda_stream);
 
-/* Statistics of g.  Host output. */
+/* Statistics of g (Sec. 3: n, |E+|, |W+| = sum C(d+,2), max d+; the paper
+ * reports the same figures per dataset in Table 2), in one struct rather
+ * than separate out-parameters.  *info: host, written on success.  Errors:
+ * INVALID_ARG for a NULL handle or info.  No device work. */
 int tripoll_graph_stats(tripoll_graph_t g, tripoll_graph_info* info);
 
 /* Number of wedge checks (Sec. 3: a wedge (p,q),(p,r) with q <+ r, checked for
@@ -225,8 +247,11 @@ int tripoll_wedge_checks(tripoll_graph_t g, uint32_t t_lo, uint32_t t_hi, uint64
 int tripoll_graph_export(tripoll_graph_t g, uint64_t* offsets, uint32_t* col, uint32_t* ts,
                          uint8_t* elabel, uint32_t* order, void* cuda_stream);
 
-/* Release the graph's device memory.  The caller must not destroy a graph
- * while surveys on it may still run on some stream. */
+/* Release the graph's device memory: the arrays of G+ and Adj+^m (Sec. 4.2)
+ * and the survey plan, each returned to the allocator that made it, ordered on
+ * the legacy default stream.  The caller must not destroy a graph while
+ * surveys on it may still run on some stream, nor while a server holds it.
+ * NULL is ignored; no status. */
 void tripoll_destroy(tripoll_graph_t g);
 
 /* ---- serving: resident graphs, continuous batching of survey requests ----
@@ -257,6 +282,35 @@ void tripoll_server_destroy(tripoll_server_t s);
 /* Number of the library's own kernels launched by this process so far (not
  * counting launches made inside CUB routines).  For launch accounting only. */
 uint64_t tripoll_launch_count(void);
+
+/* ---- device memory ----
+ *
+ * By default every device array and temporary of the library comes from a
+ * stream-ordered memory pool private to the library (one per device; it keeps
+ * up to a quarter of the device's memory, at most 64 GiB, cached between
+ * calls).  The caller's default pool and its settings are not touched.
+ *
+ * tripoll_set_allocator installs the caller's allocator instead -- e.g. a
+ * framework's caching allocator, so that the library draws from the memory the
+ * framework already holds (a library hook; the paper, whose method runs on
+ * host memory, has no counterpart).  alloc(bytes, stream, ctx) returns device memory of the
+ * current device, at least 256-byte aligned, that work ordered on `stream`
+ * after the call may use, or NULL when it cannot (the library then fails with
+ * TRIPOLL_ERR_NO_MEMORY and returns everything it holds; memory that is not
+ * 256-byte aligned is handed back to free_fn and treated the same way).  free_fn(ptr, bytes,
+ * stream, ctx) takes back one allocation; work ordered on `stream` before the
+ * call may still be using it.  Graph arrays are returned on the legacy default
+ * stream (NULL) by tripoll_destroy.  Both functions may be called from any
+ * thread, including the server's dispatcher thread.  Every allocation is
+ * returned to the allocator that made it, even after another one has been
+ * installed.  Passing alloc == NULL (with free_fn == NULL) restores the
+ * library's pool.  Install the allocator before the calls that should use it;
+ * changing it while other threads call the library is allowed but which
+ * allocator an in-flight call uses is then unspecified.
+ *   Errors: INVALID_ARG when exactly one of alloc, free_fn is NULL. */
+typedef void* (*tripoll_alloc_fn)(size_t bytes, void* cuda_stream, void* ctx);
+typedef void (*tripoll_free_fn)(void* ptr, size_t bytes, void* cuda_stream, void* ctx);
+int tripoll_set_allocator(tripoll_alloc_fn alloc, tripoll_free_fn free_fn, void* ctx);
 
 /* Human-readable text of a status, and the detail of the calling thread's
  * last error (static storage; never NULL). */

@@ -45,8 +45,13 @@ EXPORTS = (
     "tripoll_survey_range", "tripoll_partition_pivots", "tripoll_graph_stats", "tripoll_graph_export",
     "tripoll_destroy", "tripoll_server_create", "tripoll_server_add_graph", "tripoll_server_submit",
     "tripoll_server_wait", "tripoll_server_destroy", "tripoll_status_string", "tripoll_last_error",
-    "tripoll_launch_count", "tripoll_wedge_checks", "tripoll_survey_static",
+    "tripoll_launch_count", "tripoll_wedge_checks", "tripoll_survey_static", "tripoll_set_allocator",
+    "tripoll_survey_timed",
 )
+
+# C signatures of the allocator hook (tripoll_alloc_fn, tripoll_free_fn)
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 
 
 class TripollError(RuntimeError):
@@ -104,12 +109,15 @@ def load_library(path: str = LIB_PATH):
     lib.tripoll_last_error.restype = ctypes.c_char_p
     lib.tripoll_wedge_checks.argtypes = [vp, u32, u32, ctypes.POINTER(u64), vp]
     lib.tripoll_survey_static.argtypes = [vp, u32, u32, u32, vp, vp]
+    lib.tripoll_set_allocator.argtypes = [ALLOC_FN, FREE_FN, vp]
+    lib.tripoll_survey_timed.argtypes = [vp, u32, u32, u32, u64, u64, vp, vp, vp]
     lib.tripoll_launch_count.argtypes = []
     lib.tripoll_launch_count.restype = u64
     for name in ("tripoll_graph_create", "tripoll_batch_create", "tripoll_survey", "tripoll_survey_range",
                  "tripoll_partition_pivots", "tripoll_graph_stats", "tripoll_graph_export",
                  "tripoll_server_create", "tripoll_server_add_graph", "tripoll_server_submit",
-                 "tripoll_server_wait", "tripoll_wedge_checks", "tripoll_survey_static"):
+                 "tripoll_server_wait", "tripoll_wedge_checks", "tripoll_survey_static", "tripoll_set_allocator",
+                 "tripoll_survey_timed"):
         getattr(lib, name).restype = i32
     _lib = lib
     return lib
@@ -212,6 +220,15 @@ def tripoll_survey_range(g, kind_mask, t_lo, t_hi, pivot_lo, pivot_hi, result, s
     return result
 
 
+def tripoll_survey_timed(g, kind_mask, t_lo, t_hi, pivot_lo, pivot_hi, result, stream=None):
+    """tripoll_survey_range that also returns the device time (ms) of its four phases: window view,
+    warp-item kernel, block-item kernel, long-list kernel.  Synchronises the stream."""
+    ms = (ctypes.c_float * 4)()
+    _check(load_library().tripoll_survey_timed(g, kind_mask, t_lo, t_hi, pivot_lo, pivot_hi, _ptr(result), ms,
+                                               _stream(stream)), "tripoll_survey_timed")
+    return [float(x) for x in ms]
+
+
 def tripoll_partition_pivots(g, parts, stream=None):
     bounds = np.zeros(parts + 1, np.uint64)
     _check(load_library().tripoll_partition_pivots(g, parts, bounds.ctypes.data, _stream(stream)),
@@ -284,6 +301,36 @@ def tripoll_server_wait(s, request_id, result, timeout_ms=60000):
 def tripoll_server_destroy(s):
     if s:
         load_library().tripoll_server_destroy(s)
+
+
+_allocator_refs = []  # installed ctypes callbacks: they stay alive, since graphs may outlive a swap
+
+
+def tripoll_set_allocator(alloc=None, free=None):
+    """Install Python callables as the library's device allocator (see tripoll.h):
+    alloc(bytes, stream) -> device address (int), or 0 / None when it cannot;
+    free(ptr, bytes, stream).  Both None restores the library's own pool."""
+    lib = load_library()
+    a = ALLOC_FN() if alloc is None else ALLOC_FN(lambda nbytes, stream, ctx: alloc(nbytes, stream or 0) or None)
+    f = FREE_FN() if free is None else FREE_FN(lambda ptr, nbytes, stream, ctx: free(ptr, nbytes, stream or 0))
+    _check(lib.tripoll_set_allocator(a, f, None), "tripoll_set_allocator")
+    if alloc is not None:
+        _allocator_refs.append((a, f))
+
+
+def torch_caching_allocator():
+    """(alloc, free) drawing device memory from torch's caching allocator, for
+    tripoll_set_allocator: blocks are taken on the library's stream and handed back to
+    torch, which reuses them in that stream's order."""
+    import torch
+
+    def alloc(nbytes, stream):
+        return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(), int(stream))
+
+    def free(ptr, nbytes, stream):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    return alloc, free
 
 
 def tripoll_status_string(status):

@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -28,6 +29,85 @@ int fail(int status, const std::string& msg) {
 int cuda_fail(cudaError_t e, const char* what) {
     g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
     return e == cudaErrorMemoryAllocation ? TRIPOLL_ERR_NO_MEMORY : TRIPOLL_ERR_CUDA;
+}
+
+// ---- device memory ----------------------------------------------------------------------------
+
+namespace {
+std::mutex g_alloc_mu;
+Allocator g_allocator;  // alloc == nullptr: the library's pool
+
+constexpr int kMaxPoolDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kMaxPoolDevices] = {};
+
+// The library's own stream-ordered pool on device `dev`, created on first use.  It keeps up to a
+// quarter of the device's memory (at most 64 GiB) cached between calls, so that repeated builds
+// and surveys do not return memory to the driver and map it again.
+cudaError_t library_pool(int dev, cudaMemPool_t* out) {
+    if (dev < 0 || dev >= kMaxPoolDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool;
+        cudaError_t e = cudaMemPoolCreate(&pool, &props);
+        if (e != cudaSuccess) return e;
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+            uint64_t thr = std::min<uint64_t>(total_b / 4, 64ull << 30);
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+        cudaGetLastError();
+        g_pool[dev] = pool;
+    }
+    *out = g_pool[dev];
+    return cudaSuccess;
+}
+}  // namespace
+
+Allocator current_allocator() {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    return g_allocator;
+}
+
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s, const Allocator& a) {
+    *p = nullptr;
+    if (a.alloc) {
+        void* q = a.alloc(bytes, (void*)s, a.ctx);
+        if (!q) return cudaErrorMemoryAllocation;
+        if (reinterpret_cast<uintptr_t>(q) & 255u) {  // the stated alignment (vector loads rely on it)
+            a.free(q, bytes, (void*)s, a.ctx);
+            return cudaErrorMemoryAllocation;
+        }
+        *p = q;
+        return cudaSuccess;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    cudaMemPool_t pool;
+    if ((e = library_pool(dev, &pool)) != cudaSuccess) return e;
+    return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
+void dev_free(void* p, size_t bytes, cudaStream_t s, const Allocator& a) {
+    if (!p) return;
+    if (a.alloc) a.free(p, bytes, (void*)s, a.ctx);
+    else cudaFreeAsync(p, s);
+}
+
+void swap_block(tripoll_graph* g, void* graph_ptr, Scratch& sc) {
+    for (Block& b : g->blocks)
+        if (b.ptr == graph_ptr) {
+            std::swap(b.ptr, sc.ptr);
+            std::swap(b.bytes, sc.bytes);
+            std::swap(b.al, sc.al);
+            return;
+        }
 }
 
 bool is_device_pointer(const void* p) {
@@ -60,9 +140,9 @@ int check_survey_args(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uin
     return TRIPOLL_OK;
 }
 
-// Survey into `result` (device or host), pivots [p_lo, p_hi).
+// Survey into `result` (device or host), pivots [p_lo, p_hi); ev as in launch_survey.
 int survey_into(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_t t_hi, uint64_t p_lo, uint64_t p_hi,
-                uint64_t* result, cudaStream_t s) {
+                uint64_t* result, cudaStream_t s, cudaEvent_t* ev = nullptr) {
     int rc = check_survey_args(g, kinds, t_lo, t_hi, result);
     if (rc) return rc;
     const Layout lay = make_layout(kinds, g->Lv, g->Le, g->n, g->m);
@@ -77,7 +157,7 @@ int survey_into(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_t 
     }
     TP_CUDA(cudaMemsetAsync(a, 0, words * 8, s));
     if (p_hi > g->n) p_hi = g->n;
-    if (p_lo < p_hi && (rc = launch_survey(g, kinds, t_lo, t_hi, p_lo, p_hi, a, ctr.as<uint32_t>(), s)))
+    if (p_lo < p_hi && (rc = launch_survey(g, kinds, t_lo, t_hi, p_lo, p_hi, a, ctr.as<uint32_t>(), s, true, ev)))
         return rc;
     if (!dev_result) {
         TP_CUDA(cudaMemcpyAsync(result, a, words * 8, cudaMemcpyDeviceToHost, s));
@@ -148,6 +228,16 @@ extern "C" int tripoll_wedge_checks(tripoll_graph_t g, uint32_t t_lo, uint32_t t
     return TRIPOLL_OK;
 }
 
+extern "C" int tripoll_set_allocator(tripoll_alloc_fn alloc, tripoll_free_fn free_fn, void* ctx) {
+    if ((alloc == nullptr) != (free_fn == nullptr))
+        return fail(TRIPOLL_ERR_INVALID_ARG, "alloc and free_fn must both be set or both be NULL");
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_allocator.alloc = alloc;
+    g_allocator.free = free_fn;
+    g_allocator.ctx = alloc ? ctx : nullptr;
+    return TRIPOLL_OK;
+}
+
 extern "C" const char* tripoll_status_string(int status) {
     switch (status) {
         case TRIPOLL_OK: return "ok";
@@ -182,6 +272,31 @@ extern "C" int tripoll_survey_range(tripoll_graph_t g, uint32_t kind_mask, uint3
                                     uint64_t pivot_lo, uint64_t pivot_hi, uint64_t* result, void* cuda_stream) {
     if (pivot_lo > pivot_hi) return fail(TRIPOLL_ERR_INVALID_ARG, "pivot_lo > pivot_hi");
     return survey_into(g, kind_mask, t_lo, t_hi, pivot_lo, pivot_hi, result, (cudaStream_t)cuda_stream);
+}
+
+extern "C" int tripoll_survey_timed(tripoll_graph_t g, uint32_t kind_mask, uint32_t t_lo, uint32_t t_hi,
+                                    uint64_t pivot_lo, uint64_t pivot_hi, uint64_t* result, float* phase_ms,
+                                    void* cuda_stream) {
+    if (!phase_ms) return fail(TRIPOLL_ERR_INVALID_ARG, "phase_ms is NULL");
+    if (pivot_lo > pivot_hi) return fail(TRIPOLL_ERR_INVALID_ARG, "pivot_lo > pivot_hi");
+    int rc = check_survey_args(g, kind_mask, t_lo, t_hi, result);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    cudaEvent_t ev[5] = {};
+    struct Events {  // destroyed on every path
+        cudaEvent_t* e;
+        ~Events() {
+            for (int k = 0; k < 5; ++k)
+                if (e[k]) cudaEventDestroy(e[k]);
+        }
+    } guard{ev};
+    for (int k = 0; k < 5; ++k) TP_CUDA(cudaEventCreate(&ev[k]));
+    // phases that do not run still get their boundary recorded: an empty phase reads 0
+    for (int k = 0; k < 5; ++k) TP_CUDA(cudaEventRecord(ev[k], s));
+    if ((rc = survey_into(g, kind_mask, t_lo, t_hi, pivot_lo, pivot_hi, result, s, ev))) return rc;
+    TP_CUDA(cudaStreamSynchronize(s));
+    for (int k = 0; k < 4; ++k) TP_CUDA(cudaEventElapsedTime(&phase_ms[k], ev[k], ev[k + 1]));
+    return TRIPOLL_OK;
 }
 
 extern "C" int tripoll_partition_pivots(tripoll_graph_t g, uint32_t parts, uint64_t* bounds, void* cuda_stream) {

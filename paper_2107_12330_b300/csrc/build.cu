@@ -330,21 +330,6 @@ struct Input {
     }
 };
 
-// Graph arrays come from the device's stream-ordered pool, which keeps up to a
-// quarter of device memory (at most 64 GiB) cached between builds.
-template <class T> cudaError_t dalloc(T** p, uint64_t count, cudaStream_t s) {
-    return cudaMallocAsync((void**)p, std::max<uint64_t>(count, 1) * sizeof(T), s);
-}
-
-void retain_pool_memory(int dev) {
-    cudaMemPool_t pool;
-    if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) { cudaGetLastError(); return; }
-    size_t free_b = 0, total_b = 0;
-    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { cudaGetLastError(); return; }
-    uint64_t thr = std::min<uint64_t>(total_b / 4, 64ull << 30);
-    if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr) != cudaSuccess) cudaGetLastError();
-}
-
 struct GraphGuard {  // frees a half-built graph on any error path, after the stream's work
     tripoll_graph* g;
     cudaStream_t s;
@@ -373,7 +358,6 @@ int build_impl(const uint32_t* src_h, const uint32_t* dst_h, const uint32_t* ts_
 
     int dev = 0;
     TP_CUDA(cudaGetDevice(&dev));
-    retain_pool_memory(dev);
     Input src, dst, ts, el, vl;
     int rc;
     if ((rc = src.bind(src_h, m_in * 4, s)) || (rc = dst.bind(dst_h, m_in * 4, s)) ||
@@ -469,10 +453,8 @@ int build_impl(const uint32_t* src_h, const uint32_t* dst_h, const uint32_t* ts_
         // keep the buffers holding the unique arrays, drop the other two
         Scratch& kk = ukey == k0.as<uint64_t>() ? k0 : k1;
         Scratch& vv = uval == v0.as<uint64_t>() ? v0 : v1;
-        std::swap(ukey_d.ptr, kk.ptr);
-        std::swap(ukey_d.stream, kk.stream);
-        std::swap(uval_d.ptr, vv.ptr);
-        std::swap(uval_d.stream, vv.stream);
+        ukey_d.swap(kk);
+        uval_d.swap(vv);
     }
     g->m = m;
 
@@ -499,9 +481,9 @@ int build_impl(const uint32_t* src_h, const uint32_t* dst_h, const uint32_t* ts_
     if (gb + bd + b > 64) return fail(TRIPOLL_ERR_INVALID_ARG, "graph/degree/id key exceeds 64 bits");
     Scratch rank_d;
     TP_CUDA(rank_d.alloc((n + 1) * 4, s));
-    TP_CUDA(dalloc(&g->order, n, s));
-    TP_CUDA(dalloc(&g->deg, n, s));
-    if (batched) TP_CUDA(dalloc(&g->graph_of, n, s));
+    TP_CUDA(galloc(g, &g->order, n, s));
+    TP_CUDA(galloc(g, &g->deg, n, s));
+    if (batched) TP_CUDA(galloc(g, &g->graph_of, n, s));
     {
         Scratch a, c, tmp;
         TP_CUDA(a.alloc(n * 8, s));
@@ -524,20 +506,20 @@ int build_impl(const uint32_t* src_h, const uint32_t* dst_h, const uint32_t* ts_
     deg_d.release();
 
     // vertex labels in position order
-    TP_CUDA(dalloc(&g->vl, n, s));
+    TP_CUDA(galloc(g, &g->vl, n, s));
     if (n)
         vlabel_pos_kernel<<<grid_for(n), kThreads, 0, s>>>((const uint8_t*)vl.dptr, g->order, n, g->vl); ::tp::note_launch();
     TP_CUDA(cudaGetLastError());
 
     // 5. orient + CSR of G+ (col padded by kColPad entries so 32-byte vector loads
     //    of the last out-lists stay inside the allocation)
-    TP_CUDA(dalloc(&g->off, n + 1, s));
-    TP_CUDA(dalloc(&g->col, m + kColPad, s));
+    TP_CUDA(galloc(g, &g->off, n + 1, s));
+    TP_CUDA(galloc(g, &g->col, m + kColPad, s));
     TP_CUDA(cudaMemsetAsync(g->col + m, 0xFF, kColPad * 4, s));
-    TP_CUDA(dalloc(&g->ts, m + kColPad, s));  // padded like col: 16-byte loads of the last quads
-    if (g->has_el) TP_CUDA(dalloc(&g->el, m + kColPad, s));
-    TP_CUDA(dalloc(&g->in_off, n + 1, s));
-    TP_CUDA(dalloc(&g->in_edge, m, s));
+    TP_CUDA(galloc(g, &g->ts, m + kColPad, s));  // padded like col: 16-byte loads of the last quads
+    if (g->has_el) TP_CUDA(galloc(g, &g->el, m + kColPad, s));
+    TP_CUDA(galloc(g, &g->in_off, n + 1, s));
+    TP_CUDA(galloc(g, &g->in_edge, m, s));
     {
         Scratch ok0, ok1, ov1, first, cnt, tmp;
         TP_CUDA(ok0.alloc(m * 8, s));
@@ -583,9 +565,8 @@ int build_impl(const uint32_t* src_h, const uint32_t* dst_h, const uint32_t* ts_
         TP_CUDA(tmp3.alloc(tb3, s));
         TP_CUDA(cub::DeviceRadixSort::SortPairs(tmp3.ptr, tb3, ckb, reb, m, 0, tbits, s));
         if (reb.Current() != g->in_edge) {  // the sorted records are in the second buffer: keep that one
-            void* first_buf = g->in_edge;
+            swap_block(g, g->in_edge, rec1);
             g->in_edge = reb.Current();
-            rec1.ptr = first_buf;
         }
         // in-edge offsets from the runs of equal targets
         TP_CUDA(out_offsets(ckb.Current(), m, 0, n, first.as<uint32_t>(), cnt.as<uint32_t>(), g->in_off, tmp.ptr, tb,
@@ -595,7 +576,7 @@ int build_impl(const uint32_t* src_h, const uint32_t* dst_h, const uint32_t* ts_
 
     // 6. batched: vertex base of every graph
     if (batched) {
-        TP_CUDA(dalloc(&g->graph_vbase, G + 1, s));
+        TP_CUDA(galloc(g, &g->graph_vbase, G + 1, s));
         TP_CUDA(cudaMemcpyAsync(g->graph_vbase, vbase_h.data(), (G + 1) * 8ull, cudaMemcpyHostToDevice, s));
     }
 
@@ -636,12 +617,10 @@ int build_impl(const uint32_t* src_h, const uint32_t* dst_h, const uint32_t* ts_
 
 }  // namespace
 
-// Arrays return to the pool in the order of the legacy default stream.
+// Arrays go back to their allocators in the order of the legacy default stream.
 void free_graph_arrays(tripoll_graph* g) {
-    void* arrays[] = {g->off, g->col, g->ts, g->el, g->vl, g->deg, g->order, g->graph_of, g->in_off,
-                      g->in_edge, g->items_warp, g->items_block, g->items_big, g->graph_vbase};
-    for (void* a : arrays)
-        if (a) cudaFreeAsync(a, 0);
+    for (const Block& b : g->blocks) dev_free(b.ptr, b.bytes, 0, b.al);
+    g->blocks.clear();
     g->off = nullptr; g->col = nullptr; g->ts = nullptr; g->el = nullptr; g->vl = nullptr;
     g->deg = nullptr; g->order = nullptr; g->graph_of = nullptr; g->in_off = nullptr;
     g->in_edge = nullptr; g->items_warp = nullptr; g->items_block = nullptr; g->items_big = nullptr;

@@ -6,6 +6,8 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "../../include/tripoll.h"
 
@@ -25,24 +27,55 @@ int cuda_fail(cudaError_t e, const char* what);
 
 // ---- device memory owned by the library --------------------------------------------------------
 
+// Every device allocation of the library goes through dev_alloc / dev_free.  By default the
+// memory comes from a stream-ordered pool private to the library (one per device), so the
+// caller's default pool and its settings are left as they are; tripoll_set_allocator installs
+// the caller's functions instead.  An allocation remembers the allocator that made it and is
+// returned to that one, even if another allocator has been installed since.
+struct Allocator {
+    tripoll_alloc_fn alloc = nullptr;  // null: the library's own pool
+    tripoll_free_fn free = nullptr;
+    void* ctx = nullptr;
+};
+Allocator current_allocator();
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s, const Allocator& a);
+void dev_free(void* p, size_t bytes, cudaStream_t s, const Allocator& a);
+
 // Stream-ordered temporary: freed on the stream when it goes out of scope.
 struct Scratch {
     void* ptr = nullptr;
+    size_t bytes = 0;
     cudaStream_t stream = nullptr;
+    Allocator al;
     Scratch() = default;
     Scratch(const Scratch&) = delete;
     Scratch& operator=(const Scratch&) = delete;
     ~Scratch() { release(); }
-    cudaError_t alloc(size_t bytes, cudaStream_t s) {
+    cudaError_t alloc(size_t n, cudaStream_t s) {
         release();
         stream = s;
-        return cudaMallocAsync(&ptr, bytes ? bytes : 16, s);
+        bytes = n ? n : 16;
+        al = current_allocator();
+        return dev_alloc(&ptr, bytes, s, al);
     }
     void release() {
-        if (ptr) cudaFreeAsync(ptr, stream);
+        if (ptr) dev_free(ptr, bytes, stream, al);
         ptr = nullptr;
     }
+    void swap(Scratch& o) {
+        std::swap(ptr, o.ptr);
+        std::swap(bytes, o.bytes);
+        std::swap(stream, o.stream);
+        std::swap(al, o.al);
+    }
     template <class T> T* as() const { return static_cast<T*>(ptr); }
+};
+
+// A device array owned by a graph (released by free_graph_arrays).
+struct Block {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    Allocator al;
 };
 
 // Count of the library's own kernel launches (tripoll_launch_count).
@@ -127,6 +160,8 @@ struct tripoll_graph {
     uint64_t n_items_warp = 0, n_items_block = 0, n_items_big = 0;
     // statistics
     tripoll_graph_info info{};
+    // every device array above, with the allocator that made it
+    std::vector<tp::Block> blocks;
 
     tp::GraphDev dev() const {
         tp::GraphDev g;
@@ -164,11 +199,26 @@ int build_plan(tripoll_graph* g, cudaStream_t s);
 // counters: device uint32[4] of scratch.  With window_view, a window that is
 // not [0, 0xFFFFFFFF] first compacts G+ to its in-window edges in pool memory
 // (window_view_bytes of it); without, out-of-window edges are skipped in place.
+// ev (optional, 5 events): recorded on s at the phase boundaries -- start, window
+// view built, warp-item kernel done, block-item kernel done, long-list kernel done.
 int launch_survey(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_t t_hi, uint64_t p_lo,
                   uint64_t p_hi, unsigned long long* acc, uint32_t* counters, cudaStream_t s,
-                  bool window_view = true);
+                  bool window_view = true, cudaEvent_t* ev = nullptr);
 // Device scratch the window view of g takes for [t_lo, t_hi] (0 for the full window).
 uint64_t window_view_bytes(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_t t_hi);
+// Allocate count elements of T for graph g on stream s (recorded in g->blocks).
+template <class T> cudaError_t galloc(tripoll_graph* g, T** p, uint64_t count, cudaStream_t s) {
+    Block b;
+    b.bytes = (count ? count : 1) * sizeof(T);
+    b.al = current_allocator();
+    cudaError_t e = dev_alloc(&b.ptr, b.bytes, s, b.al);
+    if (e != cudaSuccess) return e;
+    g->blocks.push_back(b);
+    *p = static_cast<T*>(b.ptr);
+    return cudaSuccess;
+}
+// Exchange the graph's array at `graph_ptr` with the scratch buffer `s` (both stay owned).
+void swap_block(tripoll_graph* g, void* graph_ptr, Scratch& s);
 int check_survey_args(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_t t_hi, const void* result);
 void free_graph_arrays(tripoll_graph* g);
 }  // namespace tp

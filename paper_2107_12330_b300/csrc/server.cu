@@ -38,6 +38,7 @@ uint64_t now_ns() {
 
 struct Request {
     uint64_t id = 0;
+    const tripoll_graph* graph = nullptr;  // read under the lock at submit time
     uint32_t slot = 0, kinds = 0, t_lo = 0, t_hi = 0;
     uint64_t words = 0;
     uint64_t bytes = 0;          // device scratch charged to the budget
@@ -90,18 +91,17 @@ void CUDART_CB on_request_done(void* arg) {
 
 // Launch one admitted request on a stream (called by the dispatcher, lock not held).
 int launch_request(tripoll_server* s, Request* r, cudaStream_t st) {
-    tripoll_graph* g = s->graphs[r->slot];
-    unsigned long long* acc = nullptr;
-    TP_CUDA(cudaMallocAsync((void**)&acc, r->words * 8 + 16, st));
-    uint32_t* counters = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(acc) + r->words * 8);
-    TP_CUDA(cudaMemsetAsync(acc, 0, r->words * 8, st));
-    int rc = launch_survey(g, r->kinds, r->t_lo, r->t_hi, 0, g->n, acc, counters, st, r->view);
-    if (rc) {
-        cudaFreeAsync(acc, st);
-        return rc;
-    }
-    TP_CUDA(cudaMemcpyAsync(r->host, acc, r->words * 8, cudaMemcpyDeviceToHost, st));
-    TP_CUDA(cudaFreeAsync(acc, st));
+    (void)s;
+    const tripoll_graph* g = r->graph;
+    Scratch acc;
+    TP_CUDA(acc.alloc(r->words * 8 + 16, st));
+    unsigned long long* a = acc.as<unsigned long long>();
+    uint32_t* counters = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(a) + r->words * 8);
+    TP_CUDA(cudaMemsetAsync(a, 0, r->words * 8, st));
+    int rc = launch_survey(g, r->kinds, r->t_lo, r->t_hi, 0, g->n, a, counters, st, r->view);
+    if (rc) return rc;
+    TP_CUDA(cudaMemcpyAsync(r->host, a, r->words * 8, cudaMemcpyDeviceToHost, st));
+    acc.release();  // stream-ordered: after the copy
     TP_CUDA(cudaLaunchHostFunc(st, on_request_done, r));
     return TRIPOLL_OK;
 }
@@ -211,6 +211,7 @@ extern "C" int tripoll_server_submit(tripoll_server_t s, uint32_t slot, uint32_t
     int rc = check_survey_args(g, kind_mask, t_lo, t_hi, request_id);
     if (rc) return rc;
     Request* r = new Request();
+    r->graph = g;
     r->slot = slot;
     r->kinds = kind_mask;
     r->t_lo = t_lo;

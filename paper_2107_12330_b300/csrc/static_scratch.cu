@@ -1,14 +1,14 @@
 // static_scratch.cu -- a survey entry point that allocates no device memory.
 //
 // Some callers cannot allocate device memory at the point where they want a
-// survey: code running while its stream is being captured into a CUDA graph
-// (a cudaMalloc there is not recorded and breaks the capture), latency-bound
-// request loops that must never enter the allocator, and hosts whose device
-// memory is carved up by another framework that owns every allocation.  For
-// them tripoll_survey_static runs the same survey kernels as tripoll_survey,
-// but its scratch -- the accumulation record and the two work-item counters,
-// which tripoll_survey takes from the stream-ordered pool -- lives in the
-// fixed array below.
+// survey: latency-bound request loops that must never enter an allocator (an
+// allocation can block on the driver or on other streams), and hosts whose
+// device memory is carved up by another framework that owns every allocation.
+// For them tripoll_survey_static runs the same survey kernels as
+// tripoll_survey, but its scratch -- the accumulation record and the two
+// work-item counters, which tripoll_survey allocates -- lives in the fixed
+// array below, and a window is applied in place instead of through a
+// compacted window view.
 #include <mutex>
 
 #include "common.cuh"
@@ -29,7 +29,9 @@ std::mutex g_scratch_mu;
 void* g_scratch_addr[kMaxDevices] = {};
 
 // Device address of g_static_scratch on the current device `dev`, looked up
-// once per device (the host-side symbol is only a stand-in for it).
+// once per device (the host-side symbol is only a stand-in for it) and kept for
+// the life of the process: the device's primary context must not be reset
+// while the library is loaded.
 int scratch_address(int dev, void** out) {
     if (dev < 0 || dev >= kMaxDevices) return fail(TRIPOLL_ERR_INVALID_ARG, "device index out of range");
     std::lock_guard<std::mutex> lk(g_scratch_mu);

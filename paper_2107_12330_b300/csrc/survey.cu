@@ -922,8 +922,15 @@ int blocks_per_sm(const void* kernel, size_t smem) {
     return per;
 }
 
+// Record phase boundary k of a timed survey (no-op for an untimed one).
+inline void mark(cudaEvent_t* ev, int k, cudaStream_t s) {
+    if (ev) cudaEventRecord(ev[k], s);
+}
+
 template <int F>
-void launch_f(const tripoll_graph* g, const GraphDev& gd, const SurveyArgs& a, cudaStream_t s, int sms) {
+void launch_f(const tripoll_graph* g, const GraphDev& gd, const SurveyArgs& a, cudaStream_t s, int sms,
+              cudaEvent_t* ev) {
+    mark(ev, 1, s);
     if (g->n_items_warp) {
         size_t sm = ((a.s_words * sizeof(MirrorWord) + 15) & ~15u) + kWarps * sizeof(WarpSmem);
         const int per = blocks_per_sm((const void*)survey_warp_kernel<F>, sm);
@@ -932,6 +939,7 @@ void launch_f(const tripoll_graph* g, const GraphDev& gd, const SurveyArgs& a, c
         survey_warp_kernel<F><<<(unsigned)blocks, kBlockThreads, sm, s>>>(gd, g->items_warp,
                                                                          (uint32_t)g->n_items_warp, a); ::tp::note_launch();
     }
+    mark(ev, 2, s);
     if (g->n_items_block) {
         size_t sm = ((a.s_words * sizeof(MirrorWord) + 15) & ~15u) + block_smem_fixed<F, kBlockChunk>();
         const int per = blocks_per_sm((const void*)survey_block_kernel<F, kBlockChunk, 1>, sm);
@@ -939,6 +947,7 @@ void launch_f(const tripoll_graph* g, const GraphDev& gd, const SurveyArgs& a, c
         survey_block_kernel<F, kBlockChunk, 1><<<(unsigned)blocks, kBlockThreads, sm, s>>>(
             gd, g->items_block, (uint32_t)g->n_items_block, a); ::tp::note_launch();
     }
+    mark(ev, 3, s);
     if (g->n_items_big) {
         size_t sm = ((a.s_words * sizeof(MirrorWord) + 15) & ~15u) + block_smem_fixed<F, kBigChunk>();
         const int per = blocks_per_sm((const void*)survey_block_kernel<F, kBigChunk, 2>, sm);
@@ -946,9 +955,10 @@ void launch_f(const tripoll_graph* g, const GraphDev& gd, const SurveyArgs& a, c
         survey_block_kernel<F, kBigChunk, 2><<<(unsigned)blocks, kBlockThreads, sm, s>>>(
             gd, g->items_big, (uint32_t)g->n_items_big, a); ::tp::note_launch();
     }
+    mark(ev, 4, s);
 }
 
-using LaunchFn = void (*)(const tripoll_graph*, const GraphDev&, const SurveyArgs&, cudaStream_t, int);
+using LaunchFn = void (*)(const tripoll_graph*, const GraphDev&, const SurveyArgs&, cudaStream_t, int, cudaEvent_t*);
 
 // ---- window view: G+ restricted to the edges in the window ----------------------------------
 //
@@ -1022,9 +1032,9 @@ int build_plan(tripoll_graph* g, cudaStream_t s) {
     g->n_items_warp = tot[0];
     g->n_items_block = tot[1];
     g->n_items_big = tot[2];
-    TP_CUDA(cudaMallocAsync((void**)&g->items_warp, std::max<uint64_t>(1, tot[0]) * sizeof(WorkItem), s));
-    TP_CUDA(cudaMallocAsync((void**)&g->items_block, std::max<uint64_t>(1, tot[1]) * sizeof(WorkItem), s));
-    TP_CUDA(cudaMallocAsync((void**)&g->items_big, std::max<uint64_t>(1, tot[2]) * sizeof(WorkItem), s));
+    TP_CUDA(galloc(g, &g->items_warp, std::max<uint64_t>(1, tot[0]), s));
+    TP_CUDA(galloc(g, &g->items_block, std::max<uint64_t>(1, tot[1]), s));
+    TP_CUDA(galloc(g, &g->items_big, std::max<uint64_t>(1, tot[2]), s));
     if (n)
         plan_fill_kernel<<<grid_n(n), 256, 0, s>>>(g->off, g->in_off, n, o[0].as<uint32_t>(), o[1].as<uint32_t>(),
                                                    o[2].as<uint32_t>(), g->items_warp, g->items_block,
@@ -1043,7 +1053,7 @@ uint64_t window_view_bytes(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo
 
 // Launch the survey kernels accumulating into `acc` (zeroed by the caller).
 int launch_survey(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_t t_hi, uint64_t p_lo, uint64_t p_hi,
-                  unsigned long long* acc, uint32_t* counters, cudaStream_t s, bool window_view) {
+                  unsigned long long* acc, uint32_t* counters, cudaStream_t s, bool window_view, cudaEvent_t* ev) {
     const Layout lay = make_layout(kinds, g->Lv, g->Le, g->n, g->m);
     SurveyArgs a;
     a.kinds = kinds;
@@ -1096,6 +1106,7 @@ int launch_survey(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
     TP_CUDA(cudaMemsetAsync(counters, 0, 16, s));
+    mark(ev, 0, s);
     GraphDev gd = g->dev();
     Scratch vpos, vcol, vts, vel, vorig, vtmp;  // released (stream-ordered) after the survey kernels
     if (window && window_view && g->m) {
@@ -1121,7 +1132,7 @@ int launch_survey(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_
         gd.newpos = vpos.as<uint32_t>();
         gd.vorig = vorig.as<uint32_t>();
     }
-    kLaunch[F](g, gd, a, s, sms);
+    kLaunch[F](g, gd, a, s, sms, ev);
     TP_CUDA(cudaGetLastError());
     return TRIPOLL_OK;
 }

@@ -28,9 +28,11 @@ RECIPES = {
     "rmat22": lambda: synth.rmat(22, 1),
     # the 50M-vertex Chung-Lu recipe at 2M vertices (28 sampled pairs per vertex, as at full size)
     "chunglu2m": lambda: synth.chung_lu_50m(m_samples=56_000_000, n=2_000_000),
+    # the full 50M-vertex Chung-Lu workload (1.2G sampled pairs, about 995M unique edges)
+    "chunglu50m": lambda: synth.chung_lu_50m(),
 }
 # workloads whose result vector is stored by digest (large label-triple tables)
-DIGEST_ONLY = {"chunglu2m"}
+DIGEST_ONLY = {"chunglu2m", "chunglu50m"}
 
 
 BATCH_KINDS = synth.COUNT | synth.CLOSURE_HIST

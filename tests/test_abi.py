@@ -102,8 +102,21 @@ def test_invalid_arguments_are_rejected_before_any_gpu_work():
         "partition of no graph": lambda: tp.tripoll_partition_pivots(None, 2),
         "server without budget": lambda: tp.tripoll_server_create(0, 4),
         "server without requests in flight": lambda: tp.tripoll_server_create(1 << 20, 0),
+        "allocator without its free": lambda: tp.tripoll_set_allocator(lambda n, s: 0, None),
+        "free without its allocator": lambda: tp.tripoll_set_allocator(None, lambda p, n, s: None),
     }
     for what, call in cases.items():
         with pytest.raises(tp.TripollError) as e:
             call()
         assert e.value.status == tp.TRIPOLL_ERR_INVALID_ARG, what
+
+
+def test_allocator_hook_installs_and_restores_on_the_host():
+    """Installing an allocator and restoring the library's pool are host-side settings: both succeed
+    without a device, and no allocation is made by installing one."""
+    calls = []
+    tp.tripoll_set_allocator(lambda n, s: calls.append(n) or 0, lambda p, n, s: calls.append(-1))
+    try:
+        assert calls == []
+    finally:
+        tp.tripoll_set_allocator(None, None)

@@ -1,7 +1,8 @@
 """Serving: resident graphs and continuously batched requests.  Every result a
 request gets in a mix of concurrent requests (different graphs, kinds and
 windows, submitted from several threads while others run) must equal the
-survey of that request alone, bit for bit."""
+survey of that request alone, bit for bit, and both must equal the CPU
+oracle's survey of the request (on the graphs the oracle finishes quickly)."""
 import threading
 
 import numpy as np
@@ -9,6 +10,7 @@ import pytest
 
 import synth
 import paper_2107_12330_b300 as tp
+from gpu_util import oracle_vector
 
 pytestmark = pytest.mark.gpu
 KINDS = [tp.TRIPOLL_COUNT, tp.TRIPOLL_CLOSURE_HIST, tp.TRIPOLL_VLABEL_TRIPLES, tp.TRIPOLL_ELABEL_TRIPLES,
@@ -39,11 +41,17 @@ def test_requests_in_a_mix_equal_requests_alone():
                 lo, hi = 0, 0xFFFFFFFF
             reqs.append((gi, k, lo, hi))
         alone = []
+        checked = 0
         for gi, k, lo, hi in reqs:
             g, h = graphs[gi]
             o = np.zeros(tp.tripoll_result_words(k, 16, 8, g.n), np.uint64)
             tp.tripoll_survey(h, k, lo, hi, o)
             alone.append(o)
+            if g.n <= 1 << 14:  # the request against the oracle (Sec. 3 triangle set, Alg. 4 closing time)
+                want, _ = oracle_vector(g, k, window=(lo, hi))
+                assert np.array_equal(o, want), f"request {(gi, k, lo, hi)} differs from the oracle"
+                checked += 1
+        assert checked >= 30
         srv = tp.tripoll_server_create(1 << 30, 8)
         try:
             slots = [tp.tripoll_server_add_graph(srv, h) for _, h in graphs]
@@ -93,3 +101,54 @@ def test_requests_beyond_the_scratch_budget_are_refused():
     finally:
         for _, h in graphs:
             tp.tripoll_destroy(h)
+
+
+def test_requests_without_room_for_a_window_view_match_the_oracle():
+    """A budget that holds a request's result but not the window view makes the server survey in place
+    (out-of-window edges skipped where they are met); those results must equal the oracle's too."""
+    graphs = [(g, h) for g, h in _graphs() if g.n <= 1 << 14]
+    srv = tp.tripoll_server_create(64 << 10, 4)
+    try:
+        slots = [tp.tripoll_server_add_graph(srv, h) for _, h in graphs]
+        reqs = []
+        for i in range(16):
+            d = [synth.draw(6, 3, 4 * i + j) for j in range(4)]
+            gi = d[0] % len(graphs)
+            k = KINDS[d[1] % len(KINDS)]
+            lo, hi = sorted(((d[2] >> 40) % (1 << 24), (d[3] >> 40) % (1 << 24)))
+            reqs.append((gi, k, lo, hi, tp.tripoll_server_submit(srv, slots[gi], k, lo, hi)))
+        for gi, k, lo, hi, rid in reqs:
+            g, _ = graphs[gi]
+            o = np.zeros(tp.tripoll_result_words(k, 16, 8, g.n), np.uint64)
+            tp.tripoll_server_wait(srv, rid, o, 120000)
+            want, _ = oracle_vector(g, k, window=(lo, hi))
+            assert np.array_equal(o, want), f"request {(gi, k, lo, hi)} differs from the oracle"
+    finally:
+        tp.tripoll_server_destroy(srv)
+        for _, h in graphs:
+            tp.tripoll_destroy(h)
+
+
+def test_wait_times_out_and_the_request_stays_queued():
+    """A wait shorter than the request's run returns TRIPOLL_ERR_TIMEOUT (a bounded wait on the host, no
+    GPU involvement); the request stays queued and a later wait returns its result."""
+    g = synth.rmat_graph(22, 16, 4, ts_bits=24, num_vlabels=16, num_elabels=8)
+    h = tp.tripoll_graph_create(g.src, g.dst, g.ts, g.elabel, g.vlabel, g.n, 16, 8)
+    srv = tp.tripoll_server_create(1 << 30, 4)
+    try:
+        slot = tp.tripoll_server_add_graph(srv, h)
+        k = tp.TRIPOLL_COUNT | tp.TRIPOLL_CLOSURE_HIST
+        ids = [tp.tripoll_server_submit(srv, slot, k) for _ in range(3)]
+        o = np.zeros(tp.tripoll_result_words(k, 16, 8, g.n), np.uint64)
+        with pytest.raises(tp.TripollError) as e:
+            tp.tripoll_server_wait(srv, ids[-1], o, 0)
+        assert e.value.status == tp.TRIPOLL_ERR_TIMEOUT
+        alone = np.zeros_like(o)
+        tp.tripoll_survey(h, k, 0, 0xFFFFFFFF, alone)
+        for rid in ids:
+            o[:] = 0
+            tp.tripoll_server_wait(srv, rid, o, 120000)
+            assert np.array_equal(o, alone)
+    finally:
+        tp.tripoll_server_destroy(srv)
+        tp.tripoll_destroy(h)

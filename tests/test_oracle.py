@@ -218,6 +218,16 @@ def test_invariances():
         eq(oracle.survey_graph(g, order_mode=mode, extras=("joint", "maxel", "degtri")))
 
 
+def test_degree_triples_under_a_window_use_the_whole_graphs_degrees():
+    """The window selects triangles, not degrees: d(v) is the degree in the whole simple graph (Sec. 3, Sec.
+    5.9), so a window that leaves out edges at a vertex does not change its degree bin."""
+    # triangle {0,1,2} at ts 5; edges (0,3), (0,4) at ts 50 lie outside the window [0, 10]
+    r = run([0, 1, 0, 0, 0], [1, 2, 2, 3, 4], [5, 5, 5, 50, 50], None, None, 5, 1, 1, t_lo=0, t_hi=10)
+    assert int(r["count"][0]) == 1
+    # d(0) = 4 -> bin 2; d(1) = d(2) = 2 -> bin 1: the sorted triple (1, 1, 2), not (1, 1, 1)
+    assert np.nonzero(r["degtri"])[0].tolist() == [(1 * 33 + 1) * 33 + 2]
+
+
 def test_window_equals_filtered_subgraph():
     g = synth.rmat_graph(10, 16, 8, ts_bits=10, num_vlabels=2, num_elabels=4)
     lo, hi = 200, 700
