@@ -7,8 +7,8 @@
  * What it computes (TriPoll, Sec. 3 and Sec. 4.3, Alg. 1):
  *   1. The simple undirected graph G' of the input: records with u == v are
  *      dropped; all records of one unordered pair {u,v} become one edge whose
- *      metadata (ts, elabel) is the lexicographic minimum over the records --
- *      "keep the chronologically first" (Sec. 5.2), label as the tie-break.
+ *      metadata (ts, elabel) is the lexicographic minimum over the records:
+ *      the earliest record survives (Sec. 5.2), label as the tie-break.
  *   2. Degrees d(v) in G' (Sec. 3).
  *   3. The degree order <+ : u <+ v iff d(u) < d(v), or d(u) == d(v) and
  *      tie(u) < tie(v) (Sec. 3).  tie is the vertex id (mode 0), a bijective
