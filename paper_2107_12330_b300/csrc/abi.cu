@@ -1,7 +1,5 @@
 // abi.cu -- the C entry points around the builder and the survey kernels:
 // status text, argument checks, result buffers, statistics, export, shards.
-#include <cub/cub.cuh>
-
 #include <algorithm>
 #include <atomic>
 #include <mutex>
@@ -9,6 +7,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "primitives.cuh"
 
 namespace tp {
 
@@ -310,10 +309,11 @@ extern "C" int tripoll_partition_pivots(tripoll_graph_t g, uint32_t parts, uint6
     if (n) {
         pivot_cost_kernel<<<(unsigned)std::min<uint64_t>((n + 255) / 256, 148 * 64), 256, 0, s>>>(g->off, n,
                                                                                                cost.as<uint64_t>()); ::tp::note_launch();
-        size_t tb = 0;
-        TP_CUDA(cub::DeviceScan::InclusiveSum(nullptr, tb, cost.as<uint64_t>(), prefix.as<uint64_t>(), n, s));
-        TP_CUDA(tmp.alloc(tb, s));
-        TP_CUDA(cub::DeviceScan::InclusiveSum(tmp.ptr, tb, cost.as<uint64_t>(), prefix.as<uint64_t>(), n, s));
+        TP_CUDA(tmp.alloc(prim::scan_scratch_bytes(n), s));
+        int rc;
+        if ((rc = prim::scan<uint64_t, true>(prim::Load<uint64_t, uint64_t>{cost.as<uint64_t>(), n},
+                                             prefix.as<uint64_t>(), n, tmp.ptr, s)))
+            return rc;
     }
     cut_kernel<<<(parts + 1 + 255) / 256, 256, 0, s>>>(prefix.as<uint64_t>(), n, parts, cuts.as<uint64_t>()); ::tp::note_launch();
     TP_CUDA(cudaGetLastError());

@@ -16,13 +16,12 @@
 //   in-edges   16-byte records of the same edges, stably sorted by target: for
 //              every middle vertex q the directed edges (p,q) that end at it
 //   stats      |E+|, |W+| = sum C(d+,2), d+ max, ...
-#include <cub/cub.cuh>
-
 #include <algorithm>
 #include <utility>
 #include <vector>
 
 #include "common.cuh"
+#include "primitives.cuh"
 
 namespace tp {
 namespace {
@@ -118,10 +117,6 @@ __global__ void canon_kernel(const uint32_t* __restrict__ src, const uint32_t* _
         val[i] = ((uint64_t)ts[i] << 8) | (el ? el[i] : 0u);
     }
 }
-
-struct MinOp {
-    __device__ __forceinline__ uint64_t operator()(uint64_t a, uint64_t b) const { return a < b ? a : b; }
-};
 
 __global__ void unique_count_kernel(const uint64_t* ukey, const uint64_t* runs, uint64_t sentinel, uint64_t* m_out) {
     uint64_t r = *runs;
@@ -281,19 +276,19 @@ __global__ void stats_kernel(const uint64_t* __restrict__ off, const uint64_t* _
 }
 
 // off[0..n] = exclusive prefix of the run lengths of (key >> shift) over m
-// keys sorted ascending (first, cnt: scratch of n + 1 words; tmp: scan scratch).
+// keys sorted ascending (first, cnt: scratch of n + 1 words; scr: scan scratch
+// of prim::scan_scratch_bytes(n + 1)).
 template <class K>
-cudaError_t out_offsets(const K* key, uint64_t m, int shift, uint64_t n, uint32_t* first, uint32_t* cnt, uint64_t* off,
-                        void* tmp, size_t tb, cudaStream_t s) {
-    cudaError_t e;
-    if ((e = cudaMemsetAsync(first, 0, (n + 1) * 4, s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(cnt, 0, (n + 1) * 4, s)) != cudaSuccess) return e;
+int out_offsets(const K* key, uint64_t m, int shift, uint64_t n, uint32_t* first, uint32_t* cnt, uint64_t* off,
+                void* scr, cudaStream_t s) {
+    TP_CUDA(cudaMemsetAsync(first, 0, (n + 1) * 4, s));
+    TP_CUDA(cudaMemsetAsync(cnt, 0, (n + 1) * 4, s));
     if (m) {
         run_ends_kernel<K><<<grid_for(m), kThreads, 0, s>>>(key, m, shift, first, cnt); ::tp::note_launch();
         if (n) { run_count_kernel<<<grid_for(n), kThreads, 0, s>>>(first, cnt, n); ::tp::note_launch(); }
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        TP_CUDA(cudaGetLastError());
     }
-    return cub::DeviceScan::ExclusiveSum(tmp, tb, cnt, off, n + 1, s);
+    return prim::scan<uint64_t, false>(prim::Load<uint32_t, uint64_t>{cnt, n + 1}, off, n + 1, scr, s);
 }
 
 // Device copy of a caller array that may live in host memory.
@@ -413,10 +408,11 @@ int build_impl(const uint32_t* src_h, const uint32_t* dst_h, const uint32_t* ts_
     g->has_el = el_h != nullptr;
 
     // 2. canonical keys + payloads, sort, keep min payload per key run
+    uint32_t* fault = flags_d.as<uint32_t>() + 1;  // look-back waits of the radix sorts that gave up
     uint64_t m = 0;
     Scratch ukey_d, uval_d;
     {
-        Scratch k0, k1, v0, v1, tmp, runs;
+        Scratch k0, k1, v0, v1, scr, runs;
         TP_CUDA(k0.alloc(m_in * 8, s));
         TP_CUDA(k1.alloc(m_in * 8, s));
         TP_CUDA(v0.alloc(m_in * 8, s));
@@ -427,34 +423,42 @@ int build_impl(const uint32_t* src_h, const uint32_t* dst_h, const uint32_t* ts_
                 (const uint8_t*)el.dptr, m_in, eoff, vbase, G, b, sentinel, k0.as<uint64_t>(), v0.as<uint64_t>()); ::tp::note_launch();
         TP_CUDA(cudaGetLastError());
         src.copy.release(); dst.copy.release(); ts.copy.release(); el.copy.release();
-        cub::DoubleBuffer<uint64_t> kb(k0.as<uint64_t>(), k1.as<uint64_t>());
-        cub::DoubleBuffer<uint64_t> vb(v0.as<uint64_t>(), v1.as<uint64_t>());
-        size_t tb = 0;
+        const uint64_t tiles = (m_in + prim::kTile - 1) / prim::kTile;
+        TP_CUDA(scr.alloc(std::max(prim::sort_scratch_bytes(m_in), tiles * 12 + prim::scan_scratch_bytes(tiles) + 512), s));
+        bool alt = false;
         const int end_bit = std::min(64, 2 * b);
-        TP_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tb, kb, vb, m_in, 0, end_bit, s));
-        TP_CUDA(tmp.alloc(tb, s));
-        TP_CUDA(cub::DeviceRadixSort::SortPairs(tmp.ptr, tb, kb, vb, m_in, 0, end_bit, s));
-        // reduce-by-key into the buffers not holding the sorted data
-        uint64_t* ukey = kb.Alternate();
-        uint64_t* uval = vb.Alternate();
+        if ((rc = prim::radix_sort<uint64_t, uint64_t>(k0.as<uint64_t>(), k1.as<uint64_t>(), v0.as<uint64_t>(),
+                                                         v1.as<uint64_t>(), m_in, end_bit, scr.ptr, fault, s, &alt)))
+            return rc;
+        Scratch& kc = alt ? k1 : k0;  // sorted
+        Scratch& vc = alt ? v1 : v0;
+        Scratch& ku = alt ? k0 : k1;  // unique keys and their minimum payloads go here
+        Scratch& vu = alt ? v0 : v1;
+        // the minimum payload of every run of equal keys: the chronologically first record (Sec. 5.2)
         TP_CUDA(runs.alloc(16, s));
-        size_t tb2 = 0;
-        TP_CUDA(cub::DeviceReduce::ReduceByKey(nullptr, tb2, kb.Current(), ukey, vb.Current(), uval,
-                                               runs.as<uint64_t>(), MinOp(), m_in, s));
-        if (tb2 > tb) TP_CUDA(tmp.alloc(tb2, s));
-        TP_CUDA(cub::DeviceReduce::ReduceByKey(tmp.ptr, tb2, kb.Current(), ukey, vb.Current(), uval,
-                                               runs.as<uint64_t>(), MinOp(), m_in, s));
-        if (m_in == 0) TP_CUDA(cudaMemsetAsync(runs.ptr, 0, 8, s));
-        unique_count_kernel<<<1, 1, 0, s>>>(ukey, runs.as<uint64_t>(), sentinel, runs.as<uint64_t>() + 1); ::tp::note_launch();
+        TP_CUDA(cudaMemsetAsync(runs.ptr, 0, 16, s));
+        if (m_in) {
+            uint32_t* heads = scr.as<uint32_t>();
+            uint64_t* tbase = reinterpret_cast<uint64_t*>(scr.as<unsigned char>() + (tiles * 4 + 255) / 256 * 256);
+            void* sscr = reinterpret_cast<unsigned char*>(tbase) + (tiles * 8 + 255) / 256 * 256;
+            prim::run_heads_kernel<<<(unsigned)tiles, prim::kThreads, 0, s>>>(kc.as<uint64_t>(), m_in, heads); ::tp::note_launch();
+            if ((rc = prim::scan<uint64_t, false>(prim::Load<uint32_t, uint64_t>{heads, tiles}, tbase, tiles, sscr, s,
+                                                  runs.as<uint64_t>())))
+                return rc;
+            TP_CUDA(cudaMemsetAsync(vu.ptr, 0xFF, m_in * 8, s));
+            prim::run_min_kernel<<<(unsigned)tiles, prim::kThreads, 0, s>>>(
+                kc.as<uint64_t>(), vc.as<uint64_t>(), m_in, tbase, ku.as<uint64_t>(),
+                vu.as<unsigned long long>()); ::tp::note_launch();
+            TP_CUDA(cudaGetLastError());
+        }
+        unique_count_kernel<<<1, 1, 0, s>>>(ku.as<uint64_t>(), runs.as<uint64_t>(), sentinel, runs.as<uint64_t>() + 1); ::tp::note_launch();
         TP_CUDA(cudaGetLastError());
         TP_CUDA(cudaMemcpyAsync(&m, runs.as<uint64_t>() + 1, 8, cudaMemcpyDeviceToHost, s));
         TP_CUDA(cudaStreamSynchronize(s));
         if (m >= 0xFFFFFFFFull) return fail(TRIPOLL_ERR_INVALID_ARG, "more than 2^32-2 unique edges");
         // keep the buffers holding the unique arrays, drop the other two
-        Scratch& kk = ukey == k0.as<uint64_t>() ? k0 : k1;
-        Scratch& vv = uval == v0.as<uint64_t>() ? v0 : v1;
-        ukey_d.swap(kk);
-        uval_d.swap(vv);
+        ukey_d.swap(ku);
+        uval_d.swap(vu);
     }
     g->m = m;
 
@@ -492,14 +496,15 @@ int build_impl(const uint32_t* src_h, const uint32_t* dst_h, const uint32_t* ts_
             vertex_key_kernel<<<grid_for(n), kThreads, 0, s>>>(deg_d.as<uint32_t>(), n, vbase, G, b, bd,
                                                                a.as<uint64_t>()); ::tp::note_launch();
         TP_CUDA(cudaGetLastError());
-        cub::DoubleBuffer<uint64_t> kb(a.as<uint64_t>(), c.as<uint64_t>());
-        size_t tb = 0;
         const int end_bit = gb + bd + b;
-        TP_CUDA(cub::DeviceRadixSort::SortKeys(nullptr, tb, kb, n, 0, end_bit, s));
-        TP_CUDA(tmp.alloc(tb, s));
-        TP_CUDA(cub::DeviceRadixSort::SortKeys(tmp.ptr, tb, kb, n, 0, end_bit, s));
+        TP_CUDA(tmp.alloc(prim::sort_scratch_bytes(n), s));
+        bool alt = false;
+        if ((rc = prim::radix_sort<uint64_t, prim::NoValue>(a.as<uint64_t>(), c.as<uint64_t>(), nullptr, nullptr, n,
+                                                            end_bit, tmp.ptr, fault, s, &alt)))
+            return rc;
+        const uint64_t* sorted = alt ? c.as<uint64_t>() : a.as<uint64_t>();
         if (n)
-            rank_kernel<<<grid_for(n), kThreads, 0, s>>>(kb.Current(), n, b, rank_d.as<uint32_t>(), g->order,
+            rank_kernel<<<grid_for(n), kThreads, 0, s>>>(sorted, n, b, rank_d.as<uint32_t>(), g->order,
                                                          deg_d.as<uint32_t>(), g->deg, bd + b, g->graph_of); ::tp::note_launch();
         TP_CUDA(cudaGetLastError());
     }
@@ -521,7 +526,7 @@ int build_impl(const uint32_t* src_h, const uint32_t* dst_h, const uint32_t* ts_
     TP_CUDA(galloc(g, &g->in_off, n + 1, s));
     TP_CUDA(galloc(g, &g->in_edge, m, s));
     {
-        Scratch ok0, ok1, ov1, first, cnt, tmp;
+        Scratch ok0, ok1, ov1, first, cnt, tmp, sscr;
         TP_CUDA(ok0.alloc(m * 8, s));
         TP_CUDA(ok1.alloc(m * 8, s));
         TP_CUDA(ov1.alloc(m * 8, s));
@@ -533,18 +538,18 @@ int build_impl(const uint32_t* src_h, const uint32_t* dst_h, const uint32_t* ts_
         TP_CUDA(cudaGetLastError());
         ukey_d.release();
         rank_d.release();
-        cub::DoubleBuffer<uint64_t> kb(ok0.as<uint64_t>(), ok1.as<uint64_t>());
-        cub::DoubleBuffer<uint64_t> vb(uval_d.as<uint64_t>(), ov1.as<uint64_t>());
-        size_t tb = 0, tb2 = 0;
-        TP_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tb, cnt.as<uint32_t>(), g->off, n + 1, s));
         const int end_bit = std::min(64, 2 * b);
-        TP_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tb2, kb, vb, m, 0, end_bit, s));
-        TP_CUDA(tmp.alloc(std::max(tb, tb2), s));
-        tb = tb2 = std::max(tb, tb2);
-        TP_CUDA(cub::DeviceRadixSort::SortPairs(tmp.ptr, tb2, kb, vb, m, 0, end_bit, s));
+        TP_CUDA(tmp.alloc(prim::sort_scratch_bytes(m), s));
+        TP_CUDA(sscr.alloc(prim::scan_scratch_bytes(n + 1), s));
+        bool alt = false;
+        if ((rc = prim::radix_sort<uint64_t, uint64_t>(ok0.as<uint64_t>(), ok1.as<uint64_t>(), uval_d.as<uint64_t>(),
+                                                         ov1.as<uint64_t>(), m, end_bit, tmp.ptr, fault, s, &alt)))
+            return rc;
+        const uint64_t* okey = alt ? ok1.as<uint64_t>() : ok0.as<uint64_t>();
+        const uint64_t* oval = alt ? ov1.as<uint64_t>() : uval_d.as<uint64_t>();
         // offsets: out-list lengths from the runs of equal sources, exclusive scan
-        // (m < 2^32, so 32-bit sums are exact)
-        TP_CUDA(out_offsets(kb.Current(), m, b, n, first.as<uint32_t>(), cnt.as<uint32_t>(), g->off, tmp.ptr, tb, s));
+        // (m < 2^32, so 32-bit counts are exact)
+        if ((rc = out_offsets(okey, m, b, n, first.as<uint32_t>(), cnt.as<uint32_t>(), g->off, sscr.ptr, s))) return rc;
         // CSR arrays and in-edge records in CSR order; a stable sort by target then
         // leaves the records in (target, source) order
         Scratch ck0, ck1, rec1;
@@ -552,25 +557,24 @@ int build_impl(const uint32_t* src_h, const uint32_t* dst_h, const uint32_t* ts_
         TP_CUDA(ck1.alloc(m * 4, s));
         TP_CUDA(rec1.alloc(m * sizeof(InEdge), s));
         if (m)
-            csr_fill_kernel<<<grid_for(m), kThreads, 0, s>>>(kb.Current(), vb.Current(), m, b, g->off, g->vl, g->col,
+            csr_fill_kernel<<<grid_for(m), kThreads, 0, s>>>(okey, oval, m, b, g->off, g->vl, g->col,
                                                              g->ts, g->el, g->in_edge, ck0.as<uint32_t>()); ::tp::note_launch();
         TP_CUDA(cudaGetLastError());
         ok0.release(); ok1.release(); ov1.release(); uval_d.release();
-        cub::DoubleBuffer<uint32_t> ckb(ck0.as<uint32_t>(), ck1.as<uint32_t>());
-        cub::DoubleBuffer<InEdge> reb(g->in_edge, rec1.as<InEdge>());
-        size_t tb3 = 0;
         const int tbits = std::min(32, b);
-        TP_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tb3, ckb, reb, m, 0, tbits, s));
-        Scratch tmp3;
-        TP_CUDA(tmp3.alloc(tb3, s));
-        TP_CUDA(cub::DeviceRadixSort::SortPairs(tmp3.ptr, tb3, ckb, reb, m, 0, tbits, s));
-        if (reb.Current() != g->in_edge) {  // the sorted records are in the second buffer: keep that one
+        bool ealt = false;
+        if ((rc = prim::radix_sort<uint32_t, InEdge>(ck0.as<uint32_t>(), ck1.as<uint32_t>(), g->in_edge,
+                                                       rec1.as<InEdge>(), m, tbits, tmp.ptr, fault, s, &ealt)))
+            return rc;
+        if (ealt) {  // the sorted records are in the second buffer: keep that one
+            InEdge* sorted_rec = rec1.as<InEdge>();
             swap_block(g, g->in_edge, rec1);
-            g->in_edge = reb.Current();
+            g->in_edge = sorted_rec;
         }
         // in-edge offsets from the runs of equal targets
-        TP_CUDA(out_offsets(ckb.Current(), m, 0, n, first.as<uint32_t>(), cnt.as<uint32_t>(), g->in_off, tmp.ptr, tb,
-                            s));
+        const uint32_t* ckey = ealt ? ck1.as<uint32_t>() : ck0.as<uint32_t>();
+        if ((rc = out_offsets(ckey, m, 0, n, first.as<uint32_t>(), cnt.as<uint32_t>(), g->in_off, sscr.ptr, s)))
+            return rc;
     }
     (void)vmask;
 

@@ -28,14 +28,14 @@
 // (p,q) outside the window get empty segments and entries (q,r) outside it are
 // not inserted.
 //
-// Hits are queued per warp and folded 32 at a time, one per lane; the fold
-// aggregates inside the warp with __match_any_sync, then in 32-bit words of
-// shared memory, then with 64-bit global atomics when the words are moved out
-// (rarely, and once per block at its end) -- integer adds commute, so the
-// result is exact and schedule-independent.
-#include <cub/cub.cuh>
-#include <thrust/iterator/counting_iterator.h>
-#include <thrust/iterator/transform_iterator.h>
+// Hits are queued per warp and folded 32 at a time, one per lane.  Table words
+// that fit the block's on-chip mirror of the result record get one 32-bit
+// shared-memory atomic per lane (the hardware resolves equal addresses); the
+// mirror is moved into the 64-bit record with global atomics rarely, and once
+// per block at its end.  Words outside the mirror (batched graphs, tables past
+// its size) are first merged across the warp with __match_any_sync, then
+// added with one 64-bit global atomic per distinct word.  Integer adds
+// commute, so the result is exact and schedule-independent.
 
 #include <algorithm>
 #include <map>
@@ -44,6 +44,7 @@
 #include <tuple>
 
 #include "common.cuh"
+#include "primitives.cuh"
 
 namespace tp {
 
@@ -639,8 +640,8 @@ __global__ void __launch_bounds__(kBlockThreads, CHUNK <= kBlockChunk ? 5 : 3)
                                                                      uint32_t n_items, SurveyArgs a) {
     constexpr uint32_t kBlockTable = kTableFactor * CHUNK;
     extern __shared__ __align__(16) unsigned char smem[];
-    using BlockScan = cub::BlockScan<uint32_t, kBlockThreads>;
-    __shared__ typename BlockScan::TempStorage scan_tmp;
+    static_assert(kBlockThreads == prim::kThreads, "block scan width");
+    __shared__ uint32_t scan_tmp[kWarps];
     __shared__ uint32_t s_item, s_total;
 
     MirrorWord* s_tab = reinterpret_cast<MirrorWord*>(smem);
@@ -713,8 +714,8 @@ __global__ void __launch_bounds__(kBlockThreads, CHUNK <= kBlockChunk ? 5 : 3)
             const uint32_t n_in = min(kBlockInEdges, item.in_hi - g0);
             uint32_t np = 0;
             if (threadIdx.x < n_in) np = stage_in_edge<F>(g, a, S, threadIdx.x, g0 + threadIdx.x, chunked, vlo, vhi);
-            uint32_t pre, total;
-            BlockScan(scan_tmp).ExclusiveSum(np, pre, total);
+            uint32_t total;
+            const uint32_t pre = prim::block_exclusive_scan(np, scan_tmp, &total);
             if (threadIdx.x < n_in) S.pp[threadIdx.x] = pre;
             if (threadIdx.x == 0) { S.pp[n_in] = total; s_total = total; }
             __syncthreads();
@@ -994,13 +995,7 @@ __global__ void window_view_kernel(const uint32_t* __restrict__ col, const uint3
     }
 }
 
-size_t window_scan_bytes(uint64_t m) {
-    auto flags = thrust::make_transform_iterator(thrust::counting_iterator<uint64_t>(0),
-                                                 InWindow{nullptr, m, 0u, 0u});
-    size_t tb = 0;
-    cub::DeviceScan::ExclusiveSum(nullptr, tb, flags, (uint32_t*)nullptr, m + 1);
-    return tb;
-}
+size_t window_scan_bytes(uint64_t m) { return prim::scan_scratch_bytes(m + 1); }
 constexpr LaunchFn kLaunch[16] = {&launch_f<0>,  &launch_f<1>,  &launch_f<2>,  &launch_f<3>,
                                   &launch_f<4>,  &launch_f<5>,  &launch_f<6>,  &launch_f<7>,
                                   &launch_f<8>,  &launch_f<9>,  &launch_f<10>, &launch_f<11>,
@@ -1020,12 +1015,13 @@ int build_plan(tripoll_graph* g, cudaStream_t s) {
         plan_count_kernel<<<grid_n(n), 256, 0, s>>>(g->off, g->in_off, n, c[0].as<uint32_t>(), c[1].as<uint32_t>(),
                                                     c[2].as<uint32_t>()); ::tp::note_launch();
     TP_CUDA(cudaGetLastError());
-    size_t tb = 0;
-    TP_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tb, c[0].as<uint32_t>(), o[0].as<uint32_t>(), n + 1, s));
-    TP_CUDA(tmp.alloc(tb, s));
+    TP_CUDA(tmp.alloc(prim::scan_scratch_bytes(n + 1), s));
     uint32_t tot[3] = {0, 0, 0};
+    int rc;
     for (int k = 0; k < 3; ++k) {
-        TP_CUDA(cub::DeviceScan::ExclusiveSum(tmp.ptr, tb, c[k].as<uint32_t>(), o[k].as<uint32_t>(), n + 1, s));
+        if ((rc = prim::scan<uint32_t, false>(prim::Load<uint32_t, uint32_t>{c[k].as<uint32_t>(), n + 1},
+                                              o[k].as<uint32_t>(), n + 1, tmp.ptr, s)))
+            return rc;
         TP_CUDA(cudaMemcpyAsync(&tot[k], o[k].as<uint32_t>() + n, 4, cudaMemcpyDeviceToHost, s));
     }
     TP_CUDA(cudaStreamSynchronize(s));
@@ -1116,11 +1112,10 @@ int launch_survey(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_
         TP_CUDA(vts.alloc((m + kColPad) * 4, s));
         if (g->el) TP_CUDA(vel.alloc(m + kColPad, s));
         if (kinds & TRIPOLL_EDGE_LOCAL) TP_CUDA(vorig.alloc(m * 4, s));
-        auto flags = thrust::make_transform_iterator(thrust::counting_iterator<uint64_t>(0),
-                                                     InWindow{g->ts, m, t_lo, t_hi});
-        size_t tb = window_scan_bytes(m);
-        TP_CUDA(vtmp.alloc(tb, s));
-        TP_CUDA(cub::DeviceScan::ExclusiveSum(vtmp.ptr, tb, flags, vpos.as<uint32_t>(), m + 1, s));
+        TP_CUDA(vtmp.alloc(window_scan_bytes(m), s));
+        int rc;
+        if ((rc = prim::scan<uint32_t, false>(InWindow{g->ts, m, t_lo, t_hi}, vpos.as<uint32_t>(), m + 1, vtmp.ptr, s)))
+            return rc;
         window_view_kernel<<<grid_n(m), 256, 0, s>>>(g->col, g->ts, g->el, vpos.as<uint32_t>(), m, t_lo, t_hi,
                                                      vcol.as<uint32_t>(), vts.as<uint32_t>(),
                                                      g->el ? vel.as<uint8_t>() : nullptr,
