@@ -183,6 +183,28 @@ int tripoll_survey_range(tripoll_graph_t g, uint32_t kind_mask, uint32_t t_lo, u
                          uint64_t pivot_lo, uint64_t pivot_hi, uint64_t* result,
                          void* cuda_stream);
 
+/* Several survey requests on one graph in one pass: the unit the server
+ * batches, usable on its own.  Request k surveys kinds kind_masks[k] over the
+ * window [t_lo[k], t_hi[k]] into results[k]; every result equals
+ * tripoll_survey's for that request alone.  The wedge checks (Sec. 3, Alg. 1)
+ * of the union of the windows are made once, and each triangle found is
+ * folded once -- into the cell of the requests' window bounds that holds its
+ * earliest and latest edge timestamps (Alg. 4 takes the same two times); a
+ * request's tables are the sum of the cells inside its window.
+ *   count        1..64.
+ *   kind_masks, t_lo, t_hi   host, uint32[count]; no TRIPOLL_VERTEX_LOCAL or
+ *                TRIPOLL_EDGE_LOCAL; the graph is not a batched one.
+ *   results      host, array of count pointers, each device or host memory of
+ *                tripoll_result_words(kind_masks[k], ...) words.
+ *   Scratch: the union window's view (see tripoll_survey) plus (distinct lower
+ *   bounds) x (distinct upper bounds) records of the union of the kinds.
+ *   Errors: INVALID_ARG, NO_EDGE_LABELS, NO_MEMORY (also when that record grid
+ *   would reach 2^31 words: split the requests), CUDA.  Asynchronous when every
+ *   result is device memory, else synchronises cuda_stream. */
+int tripoll_survey_many(tripoll_graph_t g, uint32_t count, const uint32_t* kind_masks,
+                        const uint32_t* t_lo, const uint32_t* t_hi, uint64_t* const* results,
+                        void* cuda_stream);
+
 /* tripoll_survey_range with the device time of each phase, for measurement:
  * CUDA events recorded on cuda_stream around each phase give phase_ms[0]
  * (building the window view), [1] (the kernel of middle vertices with short
@@ -257,14 +279,19 @@ void tripoll_destroy(tripoll_graph_t g);
 /* ---- serving: resident graphs, continuous batching of survey requests ----
  *
  * A server owns a dispatcher thread and a set of CUDA streams.  Requests
- * (graph slot, kinds, window) are admitted while their result and scratch
- * memory fit under scratch_cap_bytes and fewer than max_inflight requests are
- * on the device; admitted requests are launched together (one launch per
- * admission round, several rounds in flight on different streams), and every
- * request that arrives meanwhile joins the next round.  A windowed request is
- * charged its window view too (see tripoll_survey) when the budget holds both,
- * and otherwise runs without one.  Results are the same as tripoll_survey's
- * for that request alone. */
+ * (graph slot, kinds, window) are admitted in arrival order in rounds, while
+ * fewer than max_inflight requests are on the device and the round's device
+ * scratch fits under scratch_cap_bytes.  In a round, the requests on one graph
+ * form one batch (up to 64) that runs as one pass, as tripoll_survey_many
+ * does; a batch of one request runs as tripoll_survey.  Batches of different
+ * graphs run at once on different streams, every request that arrives
+ * meanwhile joins a later round, and a batch on a graph of 2^25 edges or more
+ * runs only when no other such batch does (the requests queue up and the next
+ * round takes them in one pass).  A batch is charged its records, its results
+ * and the window view of its (union) window when the budget holds that too;
+ * otherwise it skips out-of-window edges in place.  Results are the same as
+ * tripoll_survey's for each request alone.  Requests for local counts, and
+ * requests on batched graphs, run one per batch. */
 int tripoll_server_create(uint64_t scratch_cap_bytes, uint32_t max_inflight,
                           tripoll_server_t* out);
 /* Make g resident in the server (the server does not take ownership). */
@@ -277,6 +304,11 @@ int tripoll_server_submit(tripoll_server_t s, uint32_t slot, uint32_t kind_mask,
  * TIMEOUT when it is not done in time (it stays queued). */
 int tripoll_server_wait(tripoll_server_t s, uint64_t request_id, uint64_t* result,
                         uint64_t* latency_ns, uint32_t timeout_ms);
+/* Counters of the server so far (for measurement; no counterpart in the paper):
+ * stats[0] requests launched, [1] batches, [2] survey passes (a fused batch
+ * is one pass, a batch run request by request is one pass each), [3] requests
+ * surveyed in fused passes.  stats: host, uint64[4]. */
+int tripoll_server_stats(tripoll_server_t s, uint64_t* stats);
 void tripoll_server_destroy(tripoll_server_t s);
 
 /* Number of the library's own kernels launched by this process so far (not

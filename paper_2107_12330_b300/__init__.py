@@ -46,7 +46,7 @@ EXPORTS = (
     "tripoll_destroy", "tripoll_server_create", "tripoll_server_add_graph", "tripoll_server_submit",
     "tripoll_server_wait", "tripoll_server_destroy", "tripoll_status_string", "tripoll_last_error",
     "tripoll_launch_count", "tripoll_wedge_checks", "tripoll_survey_static", "tripoll_set_allocator",
-    "tripoll_survey_timed",
+    "tripoll_survey_timed", "tripoll_survey_many", "tripoll_server_stats",
 )
 
 # C signatures of the allocator hook (tripoll_alloc_fn, tripoll_free_fn)
@@ -111,13 +111,15 @@ def load_library(path: str = LIB_PATH):
     lib.tripoll_survey_static.argtypes = [vp, u32, u32, u32, vp, vp]
     lib.tripoll_set_allocator.argtypes = [ALLOC_FN, FREE_FN, vp]
     lib.tripoll_survey_timed.argtypes = [vp, u32, u32, u32, u64, u64, vp, vp, vp]
+    lib.tripoll_survey_many.argtypes = [vp, u32, vp, vp, vp, vp, vp]
+    lib.tripoll_server_stats.argtypes = [vp, vp]
     lib.tripoll_launch_count.argtypes = []
     lib.tripoll_launch_count.restype = u64
     for name in ("tripoll_graph_create", "tripoll_batch_create", "tripoll_survey", "tripoll_survey_range",
                  "tripoll_partition_pivots", "tripoll_graph_stats", "tripoll_graph_export",
                  "tripoll_server_create", "tripoll_server_add_graph", "tripoll_server_submit",
                  "tripoll_server_wait", "tripoll_wedge_checks", "tripoll_survey_static", "tripoll_set_allocator",
-                 "tripoll_survey_timed"):
+                 "tripoll_survey_timed", "tripoll_survey_many", "tripoll_server_stats"):
         getattr(lib, name).restype = i32
     _lib = lib
     return lib
@@ -220,6 +222,21 @@ def tripoll_survey_range(g, kind_mask, t_lo, t_hi, pivot_lo, pivot_hi, result, s
     return result
 
 
+def tripoll_survey_many(g, kind_masks, t_lo, t_hi, results, stream=None):
+    """Several requests on one graph in one pass: request k (kind_masks[k], [t_lo[k], t_hi[k]]) into
+    results[k] (each a device tensor, host tensor or numpy array of its result words)."""
+    n = len(results)
+    km = np.ascontiguousarray(kind_masks, dtype=np.uint32)
+    lo = np.ascontiguousarray(t_lo, dtype=np.uint32)
+    hi = np.ascontiguousarray(t_hi, dtype=np.uint32)
+    if not (len(km) == len(lo) == len(hi) == n):
+        raise ValueError("one kind mask, window and result per request")
+    ptrs = (ctypes.c_void_p * max(n, 1))(*[_ptr(r) for r in results])
+    _check(load_library().tripoll_survey_many(g, n, km.ctypes.data, lo.ctypes.data, hi.ctypes.data, ptrs,
+                                              _stream(stream)), "tripoll_survey_many")
+    return results
+
+
 def tripoll_survey_timed(g, kind_mask, t_lo, t_hi, pivot_lo, pivot_hi, result, stream=None):
     """tripoll_survey_range that also returns the device time (ms) of its four phases: window view,
     warp-item kernel, block-item kernel, long-list kernel.  Synchronises the stream."""
@@ -296,6 +313,13 @@ def tripoll_server_wait(s, request_id, result, timeout_ms=60000):
     _check(load_library().tripoll_server_wait(s, request_id, _ptr(result), ctypes.byref(lat), timeout_ms),
            "tripoll_server_wait")
     return lat.value
+
+
+def tripoll_server_stats(s):
+    """Server counters: requests launched, batches, survey passes, requests in fused passes."""
+    st = np.zeros(4, np.uint64)
+    _check(load_library().tripoll_server_stats(s, st.ctypes.data), "tripoll_server_stats")
+    return {"requests": int(st[0]), "batches": int(st[1]), "passes": int(st[2]), "fused_requests": int(st[3])}
 
 
 def tripoll_server_destroy(s):

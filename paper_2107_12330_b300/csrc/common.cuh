@@ -201,9 +201,27 @@ int build_plan(tripoll_graph* g, cudaStream_t s);
 // (window_view_bytes of it); without, out-of-window edges are skipped in place.
 // ev (optional, 5 events): recorded on s at the phase boundaries -- start, window
 // view built, warp-item kernel done, block-item kernel done, long-list kernel done.
+// multi (optional): several requests' windows surveyed at once -- lo, hi: their distinct lower and
+// upper bounds, ascending, at most 64 each; [t_lo, t_hi] must be [lo[0], hi.back()]; acc holds
+// lo.size() x hi.size() records of the kinds' layout (cell (i, j) at (i * hi.size() + j) * words);
+// counters has 6 + lo.size() + hi.size() words.
+struct MultiBounds {
+    std::vector<uint32_t> lo, hi;
+};
 int launch_survey(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_t t_hi, uint64_t p_lo,
                   uint64_t p_hi, unsigned long long* acc, uint32_t* counters, cudaStream_t s,
-                  bool window_view = true, cudaEvent_t* ev = nullptr);
+                  bool window_view = true, cudaEvent_t* ev = nullptr, const MultiBounds* multi = nullptr);
+// Survey `count` requests on one graph in one pass over the union of their windows (at most 64
+// requests; no local-count kinds; not a batched graph).  results[k]: device or host, sized by
+// tripoll_result_words(kinds[k], ...).  With window_view, the union window is compacted first.
+// Asynchronous when every result is device memory (or sync_host is false: the caller orders its
+// use of host results after the stream), else synchronises s.
+int survey_many(const tripoll_graph* g, uint32_t count, const uint32_t* kinds, const uint32_t* t_lo,
+                const uint32_t* t_hi, uint64_t* const* results, cudaStream_t s, bool window_view = true,
+                bool sync_host = true);
+// Device scratch survey_many takes for these requests (result records, bounds, window view).
+uint64_t survey_many_bytes(const tripoll_graph* g, uint32_t count, const uint32_t* kinds, const uint32_t* t_lo,
+                           const uint32_t* t_hi, bool window_view);
 // Device scratch the window view of g takes for [t_lo, t_hi] (0 for the full window).
 uint64_t window_view_bytes(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_t t_hi);
 // Allocate count elements of T for graph g on stream s (recorded in g->blocks).

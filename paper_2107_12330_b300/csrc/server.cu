@@ -1,18 +1,24 @@
 // server.cu -- serving loop: resident graphs, continuous batching of survey
 // requests under a scratch-memory budget.
 //
-// Requests queue on the host.  A dispatcher thread admits them in arrival
-// order while fewer than max_inflight are on the device and their scratch
-// (the device accumulator of the result) fits under the budget; each admitted
-// request is launched on one of several CUDA streams, so requests of different
-// graphs, kinds and windows overlap on the GPU.  A request on a large graph
-// (kLargeEdges edges or more) already fills the GPU, and two of them at once
-// only evict each other's working sets from L2: large requests run one at a
-// time, and small ones behind a waiting large one are admitted past it.  A
-// host function enqueued after the result copy marks the request done,
-// returns its budget and wakes the dispatcher, which admits whatever arrived
-// meanwhile.  Results are the same integer tables tripoll_survey computes for
-// the request alone.
+// Requests queue on the host.  A dispatcher thread forms admission rounds in
+// arrival order while fewer than max_inflight requests are on the device and
+// the round's scratch fits under the budget.  Within a round, requests on the
+// same graph join one batch (up to 64): a batch of several requests is one
+// pass over the graph (survey_many: the wedge checks of the union of their
+// windows once, each triangle folded once into the cell of the requests'
+// window bounds that holds it), a batch of one is an ordinary survey; batches
+// of different graphs run at once on different CUDA streams.  A batch is
+// charged what it really takes: its record grid, its results, and the window
+// view of its union window when that fits too (else the pass skips
+// out-of-window edges in place).  A batch on a large graph (kLargeEdges edges
+// or more) already fills the GPU, and two at once only evict each other's
+// working sets from L2, so large batches run one at a time while requests
+// that arrive meanwhile queue up -- the next round takes them all in one pass
+// -- and small ones are admitted past a waiting large one.  A host function
+// enqueued after a batch's result copies marks its requests done, returns the
+// budget and wakes the dispatcher.  Each result equals tripoll_survey's for
+// that request alone.
 #include <chrono>
 #include <cstring>
 #include <condition_variable>
@@ -20,6 +26,7 @@
 #include <map>
 #include <mutex>
 #include <thread>
+#include <algorithm>
 #include <unordered_map>
 #include <vector>
 
@@ -29,6 +36,12 @@ namespace tp {
 namespace {
 
 constexpr uint64_t kLargeEdges = 1ull << 25;  // graphs whose survey alone fills the GPU
+constexpr size_t kBatchMax = 64;              // requests in one pass (distinct window bounds it can hold)
+// A pass over several requests pays for every triangle of the union of their windows, while a request
+// alone pays only for those of its own; it wins when several requests share the wedge checks and every
+// triangle folds cheaply, i.e. when the whole grid of cell records fits the kernels' on-chip mirror.
+constexpr uint64_t kBatchMirrorWords = 4096;
+constexpr size_t kBatchMin = 4;               // fewer requests run one by one
 
 uint64_t now_ns() {
     return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
@@ -41,14 +54,24 @@ struct Request {
     const tripoll_graph* graph = nullptr;  // read under the lock at submit time
     uint32_t slot = 0, kinds = 0, t_lo = 0, t_hi = 0;
     uint64_t words = 0;
-    uint64_t bytes = 0;          // device scratch charged to the budget
-    bool view = false;           // survey through a window view of the graph
+    uint64_t bytes = 0;          // device scratch of the request surveyed alone
+    bool view = false;           // alone: survey through a window view of the graph
     bool large = false;          // on a graph of kLargeEdges edges or more
+    bool joins = false;          // may share a pass with other requests on its graph
     uint64_t* host = nullptr;    // pinned result buffer
     size_t host_cap = 0;
     uint64_t t_submit = 0, t_done = 0;
     int status = TRIPOLL_OK;
     bool done = false;
+};
+
+// Requests launched together: one pass over one graph.
+struct Batch {
+    std::vector<Request*> reqs;
+    const tripoll_graph* graph = nullptr;
+    uint64_t bytes = 0;  // charged to the budget
+    bool view = false;   // several requests: through the view of the union window
+    bool large = false;
     struct tripoll_server* server = nullptr;
 };
 
@@ -68,8 +91,9 @@ struct tripoll_server {
     std::unordered_map<uint64_t, tp::Request*> reqs;
     std::multimap<size_t, uint64_t*> pinned_pool;  // free pinned buffers by capacity
     uint64_t next_id = 1;
-    uint32_t inflight = 0, large_inflight = 0;
+    uint32_t inflight = 0, large_inflight = 0;  // requests, and batches on large graphs
     uint64_t in_use = 0;
+    uint64_t st_requests = 0, st_batches = 0, st_passes = 0, st_fused = 0;  // tripoll_server_stats
     bool stop = false;
     std::thread dispatcher;
 };
@@ -77,39 +101,118 @@ struct tripoll_server {
 namespace tp {
 namespace {
 
-void CUDART_CB on_request_done(void* arg) {
-    Request* r = static_cast<Request*>(arg);
-    tripoll_server* s = r->server;
+// Mark a batch's requests done and return its budget (lock not held by the caller).
+void finish_batch(Batch* b, int status) {
+    tripoll_server* s = b->server;
     std::lock_guard<std::mutex> lk(s->mu);
-    r->t_done = now_ns();
-    r->done = true;
-    s->inflight -= 1;
-    s->large_inflight -= r->large ? 1 : 0;
-    s->in_use -= r->bytes;
+    const uint64_t t = now_ns();
+    for (Request* r : b->reqs) {
+        r->status = status;
+        r->t_done = t;
+        r->done = true;
+    }
+    s->inflight -= (uint32_t)b->reqs.size();
+    s->large_inflight -= b->large ? 1 : 0;
+    s->in_use -= b->bytes;
     s->cv.notify_all();
+    delete b;
 }
 
-// Launch one admitted request on a stream (called by the dispatcher, lock not held).
-int launch_request(tripoll_server* s, Request* r, cudaStream_t st) {
-    (void)s;
-    const tripoll_graph* g = r->graph;
-    Scratch acc;
-    TP_CUDA(acc.alloc(r->words * 8 + 16, st));
-    unsigned long long* a = acc.as<unsigned long long>();
-    uint32_t* counters = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(a) + r->words * 8);
-    TP_CUDA(cudaMemsetAsync(a, 0, r->words * 8, st));
-    int rc = launch_survey(g, r->kinds, r->t_lo, r->t_hi, 0, g->n, a, counters, st, r->view);
-    if (rc) return rc;
-    TP_CUDA(cudaMemcpyAsync(r->host, a, r->words * 8, cudaMemcpyDeviceToHost, st));
-    acc.release();  // stream-ordered: after the copy
-    TP_CUDA(cudaLaunchHostFunc(st, on_request_done, r));
+void CUDART_CB on_batch_done(void* arg) { finish_batch(static_cast<Batch*>(arg), TRIPOLL_OK); }
+
+// Launch one request alone on a stream.
+int launch_single(const tripoll_graph* g, Request* r, cudaStream_t st) {
+    {
+        Scratch acc;
+        TP_CUDA(acc.alloc(r->words * 8 + 16, st));
+        unsigned long long* a = acc.as<unsigned long long>();
+        uint32_t* counters = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(a) + r->words * 8);
+        TP_CUDA(cudaMemsetAsync(a, 0, r->words * 8, st));
+        int rc = launch_survey(g, r->kinds, r->t_lo, r->t_hi, 0, g->n, a, counters, st, r->view);
+        if (rc) return rc;
+        TP_CUDA(cudaMemcpyAsync(r->host, a, r->words * 8, cudaMemcpyDeviceToHost, st));
+        acc.release();  // stream-ordered: after the copy
+    }
     return TRIPOLL_OK;
 }
 
-// May r start now?  (lock held)
+// Launch a batch on a stream (dispatcher thread, lock not held); its host function completes it.
+// A batch below kBatchMin requests runs them one after the other on the stream.
+int launch_batch(Batch* b, cudaStream_t st) {
+    const tripoll_graph* g = b->graph;
+    if (b->reqs.size() < kBatchMin) {
+        for (Request* r : b->reqs) {
+            int rc = launch_single(g, r, st);
+            if (rc) return rc;
+        }
+    } else {
+        std::vector<uint32_t> kinds, lo, hi;
+        std::vector<uint64_t*> res;
+        for (Request* r : b->reqs) {
+            kinds.push_back(r->kinds);
+            lo.push_back(r->t_lo);
+            hi.push_back(r->t_hi);
+            res.push_back(r->host);
+        }
+        // the pinned results are complete when the host function runs: no synchronisation here
+        int rc = survey_many(g, (uint32_t)b->reqs.size(), kinds.data(), lo.data(), hi.data(), res.data(), st, b->view,
+                             false);
+        if (rc) return rc;
+    }
+    TP_CUDA(cudaLaunchHostFunc(st, on_batch_done, b));
+    return TRIPOLL_OK;
+}
+
+// Scratch of a batch of several requests, with or without the union window's view (~0 when the
+// batch cannot be one pass).  Below kBatchMin the requests run one by one: their own scratch, one
+// at a time, plus each one's window view when that is what its alone-estimate holds.
+uint64_t batch_bytes(const std::vector<Request*>& reqs, bool view) {
+    std::vector<uint32_t> kinds, lo, hi;
+    uint32_t all = 0;
+    uint64_t single = 0;
+    for (Request* r : reqs) {
+        kinds.push_back(r->kinds);
+        lo.push_back(r->t_lo);
+        hi.push_back(r->t_hi);
+        all |= r->kinds;
+        single = std::max(single, r->bytes);
+    }
+    // the cell grid must fit on chip: distinct lower x upper bounds x the union layout's words
+    std::vector<uint32_t> l(lo), h(hi);
+    std::sort(l.begin(), l.end());
+    std::sort(h.begin(), h.end());
+    const uint64_t cells = (uint64_t)(std::unique(l.begin(), l.end()) - l.begin()) *
+                           (uint64_t)(std::unique(h.begin(), h.end()) - h.begin());
+    const tripoll_graph* g = reqs[0]->graph;
+    if (cells * make_layout(all, g->Lv, g->Le, g->n, g->m).words > kBatchMirrorWords) return ~0ull;
+    if (reqs.size() < kBatchMin) return single;
+    return survey_many_bytes(g, (uint32_t)reqs.size(), kinds.data(), lo.data(), hi.data(), view);
+}
+
+// May r start a batch of its own now?  (lock held)
 bool admissible(const tripoll_server* s, const Request* r) {
     if (r->large && s->large_inflight > 0) return false;
     return s->in_use + r->bytes <= s->cap || s->inflight == 0;
+}
+
+// Add r to batch b if the budget holds the larger batch (lock held).
+bool try_join(tripoll_server* s, Batch* b, Request* r) {
+    if (!r->joins || b->reqs.size() >= kBatchMax) return false;
+    std::vector<Request*> grown = b->reqs;
+    grown.push_back(r);
+    const uint64_t others = s->in_use - b->bytes;
+    bool view = true;
+    uint64_t bytes = batch_bytes(grown, true);
+    if (bytes == ~0ull || others + bytes > s->cap) {
+        view = false;
+        bytes = batch_bytes(grown, false);
+    }
+    if (bytes == ~0ull || others + bytes > s->cap) return false;
+    s->in_use = others + bytes;
+    b->bytes = bytes;
+    b->view = view;
+    b->reqs.push_back(r);
+    return true;
 }
 
 void dispatcher_loop(tripoll_server* s) {
@@ -124,21 +227,38 @@ void dispatcher_loop(tripoll_server* s) {
             return false;
         });
         if (s->stop) break;
-        // one admission round: everything that may start now, in arrival order;
-        // requests that must wait keep their place in the queue
-        std::vector<Request*> round;
+        // one admission round, in arrival order: a request joins its graph's batch of this round when
+        // the budget holds the larger batch, else starts one; requests that must wait keep their place
+        std::vector<Batch*> round;
+        std::multimap<const tripoll_graph*, Batch*> open;
         for (auto it = s->pending.begin(); it != s->pending.end() && s->inflight < s->max_inflight;) {
             Request* r = s->reqs[*it];
-            if (!admissible(s, r)) {
-                if (!r->large) break;  // over budget: keep arrival order
-                ++it;                  // a large request waits for the one running; smaller ones pass
+            bool joined = false;
+            for (auto ob = open.equal_range(r->graph); ob.first != ob.second && !joined; ++ob.first)
+                joined = try_join(s, ob.first->second, r);
+            if (joined) {
+                it = s->pending.erase(it);
+                s->inflight += 1;
                 continue;
             }
+            if (!admissible(s, r)) {
+                if (!r->large) break;  // over budget: keep arrival order
+                ++it;                  // a large request waits for the batch running; smaller ones pass
+                continue;
+            }
+            Batch* b = new Batch();
+            b->graph = r->graph;
+            b->server = s;
+            b->large = r->large;
+            b->bytes = r->bytes;
+            b->view = r->view;
+            b->reqs.push_back(r);
             it = s->pending.erase(it);
             s->inflight += 1;
             s->large_inflight += r->large ? 1 : 0;
             s->in_use += r->bytes;
-            round.push_back(r);
+            round.push_back(b);
+            if (r->joins) open.emplace(r->graph, b);
         }
         std::vector<cudaStream_t> lanes;
         for (size_t i = 0; i < round.size(); ++i) {
@@ -147,17 +267,16 @@ void dispatcher_loop(tripoll_server* s) {
         }
         lk.unlock();
         for (size_t i = 0; i < round.size(); ++i) {
-            int rc = launch_request(s, round[i], lanes[i]);
-            if (rc) {
+            {
                 std::lock_guard<std::mutex> g(s->mu);
-                round[i]->status = rc;
-                round[i]->t_done = now_ns();
-                round[i]->done = true;
-                s->inflight -= 1;
-                s->large_inflight -= round[i]->large ? 1 : 0;
-                s->in_use -= round[i]->bytes;
-                s->cv.notify_all();
+                s->st_requests += round[i]->reqs.size();
+                s->st_batches += 1;
+                const bool fused = round[i]->reqs.size() >= kBatchMin;
+                s->st_passes += fused ? 1 : round[i]->reqs.size();
+                s->st_fused += fused ? round[i]->reqs.size() : 0;
             }
+            int rc = launch_batch(round[i], lanes[i]);
+            if (rc) finish_batch(round[i], rc);
         }
         lk.lock();
     }
@@ -219,7 +338,7 @@ extern "C" int tripoll_server_submit(tripoll_server_t s, uint32_t slot, uint32_t
     r->words = make_layout(kind_mask, g->Lv, g->Le, g->n, g->m).words * g->num_graphs;
     r->bytes = r->words * 8 + 16;
     r->large = g->m >= kLargeEdges;
-    r->server = s;
+    r->joins = !g->graph_of && !(kind_mask & (TRIPOLL_VERTEX_LOCAL | TRIPOLL_EDGE_LOCAL));
     if (r->bytes > s->cap) {
         delete r;
         return fail(TRIPOLL_ERR_NO_MEMORY, "request needs more scratch than the server budget");
@@ -275,6 +394,16 @@ extern "C" int tripoll_server_wait(tripoll_server_t s, uint64_t request_id, uint
     s->pinned_pool.emplace(r->host_cap, r->host);
     delete r;
     if (status != TRIPOLL_OK) return fail(status, "request failed");
+    return TRIPOLL_OK;
+}
+
+extern "C" int tripoll_server_stats(tripoll_server_t s, uint64_t* stats) {
+    if (!s || !stats) return fail(TRIPOLL_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    stats[0] = s->st_requests;
+    stats[1] = s->st_batches;
+    stats[2] = s->st_passes;
+    stats[3] = s->st_fused;
     return TRIPOLL_OK;
 }
 

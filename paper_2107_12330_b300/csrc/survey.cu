@@ -20,6 +20,11 @@ TP_EXTERN_LAUNCH(15) TP_EXTERN_LAUNCH(16) TP_EXTERN_LAUNCH(17) TP_EXTERN_LAUNCH(
 TP_EXTERN_LAUNCH(20) TP_EXTERN_LAUNCH(21) TP_EXTERN_LAUNCH(22) TP_EXTERN_LAUNCH(23) TP_EXTERN_LAUNCH(24)
 TP_EXTERN_LAUNCH(25) TP_EXTERN_LAUNCH(26) TP_EXTERN_LAUNCH(27) TP_EXTERN_LAUNCH(28) TP_EXTERN_LAUNCH(29)
 TP_EXTERN_LAUNCH(30) TP_EXTERN_LAUNCH(31)
+// several windows at once: timestamps always, any of labels, extras and the word cache
+TP_EXTERN_LAUNCH(33) TP_EXTERN_LAUNCH(35) TP_EXTERN_LAUNCH(37) TP_EXTERN_LAUNCH(39) TP_EXTERN_LAUNCH(41)
+TP_EXTERN_LAUNCH(43) TP_EXTERN_LAUNCH(45) TP_EXTERN_LAUNCH(47) TP_EXTERN_LAUNCH(49) TP_EXTERN_LAUNCH(51)
+TP_EXTERN_LAUNCH(53) TP_EXTERN_LAUNCH(55) TP_EXTERN_LAUNCH(57) TP_EXTERN_LAUNCH(59) TP_EXTERN_LAUNCH(61)
+TP_EXTERN_LAUNCH(63)
 #undef TP_EXTERN_LAUNCH
 
 // Resident blocks per SM of a kernel at a dynamic shared-memory size; cached
@@ -178,12 +183,61 @@ __global__ void window_view_kernel(const uint32_t* __restrict__ col, const uint3
 }
 
 size_t window_scan_bytes(uint64_t m) { return prim::scan_scratch_bytes(m + 1); }
-constexpr LaunchFn kLaunch[32] = {
+constexpr LaunchFn kLaunch[64] = {
     &launch_f<0>,  &launch_f<1>,  &launch_f<2>,  &launch_f<3>,  &launch_f<4>,  &launch_f<5>,  &launch_f<6>,
     &launch_f<7>,  &launch_f<8>,  &launch_f<9>,  &launch_f<10>, &launch_f<11>, &launch_f<12>, &launch_f<13>,
     &launch_f<14>, &launch_f<15>, &launch_f<16>, &launch_f<17>, &launch_f<18>, &launch_f<19>, &launch_f<20>,
     &launch_f<21>, &launch_f<22>, &launch_f<23>, &launch_f<24>, &launch_f<25>, &launch_f<26>, &launch_f<27>,
-    &launch_f<28>, &launch_f<29>, &launch_f<30>, &launch_f<31>};
+    &launch_f<28>, &launch_f<29>, &launch_f<30>, &launch_f<31>,
+    // F_MULTI: only with F_TS (odd)
+    nullptr, &launch_f<33>, nullptr, &launch_f<35>, nullptr, &launch_f<37>, nullptr, &launch_f<39>,
+    nullptr, &launch_f<41>, nullptr, &launch_f<43>, nullptr, &launch_f<45>, nullptr, &launch_f<47>,
+    nullptr, &launch_f<49>, nullptr, &launch_f<51>, nullptr, &launch_f<53>, nullptr, &launch_f<55>,
+    nullptr, &launch_f<57>, nullptr, &launch_f<59>, nullptr, &launch_f<61>, nullptr, &launch_f<63>};
+
+// ---- several requests in one pass: cell sums -------------------------------------------------
+//
+// rec holds A x B cell records of W words.  After these two sweeps, word w of record (x, y) is the
+// sum of word w over the cells i >= x, j <= y: the tables of the request with window [L[x], H[y]].
+
+__global__ void cells_prefix_j_kernel(unsigned long long* __restrict__ rec, uint32_t A, uint32_t B, uint64_t W) {
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < (uint64_t)A * W;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t i = t / W, w = t % W;
+        unsigned long long acc = 0;
+        for (uint32_t j = 0; j < B; ++j) {
+            unsigned long long* p = rec + (i * B + j) * W + w;
+            acc += *p;
+            *p = acc;
+        }
+    }
+}
+
+__global__ void cells_suffix_i_kernel(unsigned long long* __restrict__ rec, uint32_t A, uint32_t B, uint64_t W) {
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < (uint64_t)B * W;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t j = t / W, w = t % W;
+        unsigned long long acc = 0;
+        for (uint32_t i = A; i-- > 0;) {
+            unsigned long long* p = rec + ((uint64_t)i * B + j) * W + w;
+            acc += *p;
+            *p = acc;
+        }
+    }
+}
+
+// One copy per (request, table): len words from rec + src to out + dst.
+struct TableCopy {
+    uint64_t src, dst, len;
+};
+
+__global__ void gather_tables_kernel(const unsigned long long* __restrict__ rec, const TableCopy* __restrict__ copies,
+                                     uint32_t n_copies, unsigned long long* __restrict__ out) {
+    for (uint32_t c = blockIdx.x; c < n_copies; c += gridDim.x) {
+        const TableCopy tc = copies[c];
+        for (uint64_t k = threadIdx.x; k < tc.len; k += blockDim.x) out[tc.dst + k] = rec[tc.src + k];
+    }
+}
 
 }  // namespace
 
@@ -233,8 +287,13 @@ uint64_t window_view_bytes(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo
 
 // Launch the survey kernels accumulating into `acc` (zeroed by the caller).
 int launch_survey(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_t t_hi, uint64_t p_lo, uint64_t p_hi,
-                  unsigned long long* acc, uint32_t* counters, cudaStream_t s, bool window_view, cudaEvent_t* ev) {
+                  unsigned long long* acc, uint32_t* counters, cudaStream_t s, bool window_view, cudaEvent_t* ev,
+                  const MultiBounds* multi) {
     const Layout lay = make_layout(kinds, g->Lv, g->Le, g->n, g->m);
+    if (multi && (multi->lo.empty() || multi->hi.empty() || multi->lo.size() > kMultiMax ||
+                  multi->hi.size() > kMultiMax || g->graph_of ||
+                  (kinds & (TRIPOLL_VERTEX_LOCAL | TRIPOLL_EDGE_LOCAL))))
+        return fail(TRIPOLL_ERR_INVALID_ARG, "several windows at once: 1..64 bounds, single graph, no local counts");
     SurveyArgs a;
     a.kinds = kinds;
     a.t_lo = t_lo;
@@ -260,6 +319,7 @@ int launch_survey(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_
     // record prefix mirrored on chip: the tables that fit, never the local counts
     uint64_t sw = std::min(lay.o_vlocal, lay.o_elocal);
     if (sw == ~0ull) sw = lay.words;
+    if (multi) sw = lay.words * multi->lo.size() * multi->hi.size();  // every cell's record
     if (g->graph_of) sw = 0;
     // a single record larger than the mirror: a dense prefix plus the word cache, in the same room
     const bool cache = sw > kSharedTableWords;
@@ -286,9 +346,18 @@ int launch_survey(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_
                  TRIPOLL_EDGE_LOCAL))
         F |= F_EXTRA | F_TS;
     if (cache) F |= F_CACHE;
+    if (multi) F |= F_MULTI | F_TS;
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
     TP_CUDA(cudaMemsetAsync(counters, 0, 16, s));
+    if (multi) {  // the bounds, read into shared memory by every block of the survey kernels
+        std::vector<uint32_t> b;
+        b.push_back((uint32_t)multi->lo.size());
+        b.push_back((uint32_t)multi->hi.size());
+        b.insert(b.end(), multi->lo.begin(), multi->lo.end());
+        b.insert(b.end(), multi->hi.begin(), multi->hi.end());
+        TP_CUDA(cudaMemcpyAsync(counters + 4, b.data(), b.size() * 4, cudaMemcpyHostToDevice, s));
+    }
     mark(ev, 0, s);
     GraphDev gd = g->dev();
     Scratch vpos, vcol, vts, vel, vorig, vtmp;  // released (stream-ordered) after the survey kernels
@@ -319,4 +388,130 @@ int launch_survey(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_
     return TRIPOLL_OK;
 }
 
+// ---- several requests on one graph in one pass ----------------------------------------------
+
+namespace {
+
+// Tables of a layout present in `kinds`, as (offset, length) in words, in layout order.
+void tables_of(uint32_t kinds, const Layout& L, uint32_t Lv, uint32_t Le, std::vector<std::pair<uint64_t, uint64_t>>* out) {
+    const uint64_t H = TRIPOLL_HIST_BINS;
+    if (kinds & TRIPOLL_COUNT) out->push_back({L.o_count, 1});
+    if (kinds & TRIPOLL_CLOSURE_HIST) out->push_back({L.o_hist, H});
+    if (kinds & TRIPOLL_VLABEL_TRIPLES) out->push_back({L.o_vtri, (uint64_t)Lv * Lv * Lv});
+    if (kinds & TRIPOLL_ELABEL_TRIPLES) out->push_back({L.o_etri, (uint64_t)Le * Le * Le});
+    if (kinds & TRIPOLL_OPEN_CLOSE_HIST) out->push_back({L.o_joint, H * H});
+    if (kinds & TRIPOLL_MAX_ELABEL) out->push_back({L.o_maxel, Le});
+    if (kinds & TRIPOLL_DEGREE_TRIPLES) out->push_back({L.o_degtri, H * H * H});
+}
+
+struct ManyPlan {
+    uint32_t kinds = 0;  // union
+    Layout lay;          // of the union
+    MultiBounds b;
+    std::vector<uint32_t> x, y;  // per request: index of its bounds
+    uint64_t cells = 0, rec_words = 0, out_words = 0;
+};
+
+int plan_many(const tripoll_graph* g, uint32_t count, const uint32_t* kinds, const uint32_t* t_lo,
+              const uint32_t* t_hi, ManyPlan* P) {
+    if (!g || count == 0 || !kinds || !t_lo || !t_hi) return fail(TRIPOLL_ERR_INVALID_ARG, "bad request list");
+    if (count > kMultiMax) return fail(TRIPOLL_ERR_INVALID_ARG, "at most 64 requests in one pass");
+    if (g->graph_of) return fail(TRIPOLL_ERR_INVALID_ARG, "several requests at once need a single graph");
+    for (uint32_t k = 0; k < count; ++k) {
+        int rc = check_survey_args(g, kinds[k], t_lo[k], t_hi[k], kinds);  // (result pointers checked by the caller)
+        if (rc) return rc;
+        if (kinds[k] & (TRIPOLL_VERTEX_LOCAL | TRIPOLL_EDGE_LOCAL))
+            return fail(TRIPOLL_ERR_INVALID_ARG, "local counts are surveyed one request at a time");
+        P->kinds |= kinds[k];
+        P->b.lo.push_back(t_lo[k]);
+        P->b.hi.push_back(t_hi[k]);
+        P->out_words += make_layout(kinds[k], g->Lv, g->Le, g->n, g->m).words;
+    }
+    for (auto* v : {&P->b.lo, &P->b.hi}) {
+        std::sort(v->begin(), v->end());
+        v->erase(std::unique(v->begin(), v->end()), v->end());
+    }
+    for (uint32_t k = 0; k < count; ++k) {
+        P->x.push_back((uint32_t)(std::lower_bound(P->b.lo.begin(), P->b.lo.end(), t_lo[k]) - P->b.lo.begin()));
+        P->y.push_back((uint32_t)(std::lower_bound(P->b.hi.begin(), P->b.hi.end(), t_hi[k]) - P->b.hi.begin()));
+    }
+    P->lay = make_layout(P->kinds, g->Lv, g->Le, g->n, g->m);
+    P->cells = (uint64_t)P->b.lo.size() * P->b.hi.size();
+    P->rec_words = P->cells * P->lay.words;
+    if (P->rec_words >= (1ull << 31))
+        return fail(TRIPOLL_ERR_NO_MEMORY, "too many windows x table words for one pass; split the requests");
+    return TRIPOLL_OK;
+}
+
+uint64_t many_scratch_bytes(const tripoll_graph* g, const ManyPlan& P, bool window_view) {
+    const uint64_t r = 256;
+    return (P.rec_words * 8 + r) + ((6 + P.b.lo.size() + P.b.hi.size()) * 4 + r) + (P.out_words * 8 + r) +
+           (P.x.size() * 8 * sizeof(TableCopy) + r) +
+           (window_view ? window_view_bytes(g, P.kinds, P.b.lo.front(), P.b.hi.back()) : 0);
+}
+
+}  // namespace
+
+uint64_t survey_many_bytes(const tripoll_graph* g, uint32_t count, const uint32_t* kinds, const uint32_t* t_lo,
+                           const uint32_t* t_hi, bool window_view) {
+    ManyPlan P;
+    if (plan_many(g, count, kinds, t_lo, t_hi, &P)) return ~0ull;
+    return many_scratch_bytes(g, P, window_view);
+}
+
+int survey_many(const tripoll_graph* g, uint32_t count, const uint32_t* kinds, const uint32_t* t_lo,
+                const uint32_t* t_hi, uint64_t* const* results, cudaStream_t s, bool window_view, bool sync_host) {
+    ManyPlan P;
+    int rc = plan_many(g, count, kinds, t_lo, t_hi, &P);
+    if (rc) return rc;
+    if (!results) return fail(TRIPOLL_ERR_INVALID_ARG, "results is NULL");
+    for (uint32_t k = 0; k < count; ++k)
+        if (!results[k]) return fail(TRIPOLL_ERR_INVALID_ARG, "a result pointer is NULL");
+    const uint32_t A = (uint32_t)P.b.lo.size(), B = (uint32_t)P.b.hi.size();
+    const uint64_t W = P.lay.words;
+    // copies of each request's tables out of its cell-sum record, into one packed output
+    std::vector<TableCopy> copies;
+    std::vector<uint64_t> out_off(count + 1, 0);
+    for (uint32_t k = 0; k < count; ++k) {
+        const Layout Lk = make_layout(kinds[k], g->Lv, g->Le, g->n, g->m);
+        std::vector<std::pair<uint64_t, uint64_t>> tu, tk;
+        tables_of(kinds[k], P.lay, g->Lv, g->Le, &tu);
+        tables_of(kinds[k], Lk, g->Lv, g->Le, &tk);
+        const uint64_t base = ((uint64_t)P.x[k] * B + P.y[k]) * W;
+        for (size_t t = 0; t < tu.size(); ++t) copies.push_back({base + tu[t].first, out_off[k] + tk[t].first, tu[t].second});
+        out_off[k + 1] = out_off[k] + Lk.words;
+    }
+    Scratch rec, ctr, outs, cps;
+    TP_CUDA(rec.alloc(P.rec_words * 8, s));
+    TP_CUDA(ctr.alloc((6 + A + B) * 4, s));
+    TP_CUDA(outs.alloc(out_off[count] * 8, s));
+    TP_CUDA(cps.alloc(copies.size() * sizeof(TableCopy), s));
+    TP_CUDA(cudaMemsetAsync(rec.ptr, 0, P.rec_words * 8, s));
+    TP_CUDA(cudaMemcpyAsync(cps.ptr, copies.data(), copies.size() * sizeof(TableCopy), cudaMemcpyHostToDevice, s));
+    if (g->n && (rc = launch_survey(g, P.kinds, P.b.lo.front(), P.b.hi.back(), 0, g->n, rec.as<unsigned long long>(),
+                                    ctr.as<uint32_t>(), s, window_view, nullptr, &P.b)))
+        return rc;
+    const unsigned grid_a = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((A * W + 255) / 256, 148u * 16u));
+    const unsigned grid_b = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((B * W + 255) / 256, 148u * 16u));
+    cells_prefix_j_kernel<<<grid_a, 256, 0, s>>>(rec.as<unsigned long long>(), A, B, W); note_launch();
+    cells_suffix_i_kernel<<<grid_b, 256, 0, s>>>(rec.as<unsigned long long>(), A, B, W); note_launch();
+    gather_tables_kernel<<<(unsigned)std::min<size_t>(copies.size(), 148u * 8u), 256, 0, s>>>(
+        rec.as<unsigned long long>(), cps.as<TableCopy>(), (uint32_t)copies.size(), outs.as<unsigned long long>());
+    note_launch();
+    TP_CUDA(cudaGetLastError());
+    bool host = false;
+    for (uint32_t k = 0; k < count; ++k) {
+        TP_CUDA(cudaMemcpyAsync(results[k], outs.as<unsigned long long>() + out_off[k], (out_off[k + 1] - out_off[k]) * 8,
+                                cudaMemcpyDefault, s));
+        host = host || !is_device_pointer(results[k]);
+    }
+    if (host && sync_host) TP_CUDA(cudaStreamSynchronize(s));
+    return TRIPOLL_OK;
+}
+
 }  // namespace tp
+
+extern "C" int tripoll_survey_many(tripoll_graph_t g, uint32_t count, const uint32_t* kind_masks, const uint32_t* t_lo,
+                                   const uint32_t* t_hi, uint64_t* const* results, void* cuda_stream) {
+    return tp::survey_many(g, count, kind_masks, t_lo, t_hi, results, (cudaStream_t)cuda_stream, true);
+}

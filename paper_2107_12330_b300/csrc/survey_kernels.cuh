@@ -73,6 +73,18 @@ constexpr int F_EL = 2;     // edge labels
 constexpr int F_VL = 4;     // vertex labels
 constexpr int F_EXTRA = 8;  // joint table, max label, degree triples, local counts
 constexpr int F_CACHE = 16; // record larger than the on-chip mirror: a word cache in front of global atomics
+constexpr int F_MULTI = 32; // several requests' windows at once: one record per cell of their bounds
+
+// Several requests in one pass (F_MULTI).  The distinct lower bounds L[0] < ... < L[A-1] and upper
+// bounds H[0] < ... < H[B-1] of the requests' windows cut the (earliest, latest) timestamp plane of
+// the triangles into A x B cells; a triangle with earliest timestamp t1 and latest t3 is counted in
+// cell (i, j), i the last lower bound <= t1 and j the first upper bound >= t3, whose record holds
+// all tables of the union of the requests' kinds.  The request with window [L[x], H[y]] takes
+// exactly the triangles of the cells i >= x, j <= y, so its tables are that block's sum.  The bounds
+// live in shared memory ahead of the mirror: A, B, then L and H (kMultiMax each).
+constexpr uint32_t kMultiMax = 64;
+constexpr uint32_t kMultiWords = 4 + 2 * kMultiMax;
+template <int F> __host__ __device__ constexpr uint32_t multi_bytes() { return (F & F_MULTI) ? kMultiWords * 4 : 0; }
 
 // Word cache (F_CACHE).  A record too large for the dense mirror keeps its first kCacheDenseWords
 // words dense on chip and puts a small open-addressing cache (word -> 32-bit count) in front of
@@ -100,7 +112,7 @@ struct SurveyArgs {
     uint8_t move_block_log2, move_warp_log2;
     Layout lay;  // (the argument block keeps 5 bytes of padding after the move periods)
     unsigned long long* out;  // accumulator: one record, or num_graphs records (batched)
-    uint32_t* counters;       // [3] item counters of the three kernels
+    uint32_t* counters;       // item counters of the three kernels; F_MULTI: [4] A, [5] B, then the bounds
 };
 static_assert(sizeof(SurveyArgs) == 128, "kernel argument block of the survey kernels");
 
@@ -210,44 +222,66 @@ template <int F>
 __device__ __forceinline__ void fold_warp(bool keep, const TriMeta& t, const SurveyArgs& a, MirrorWord* s_tab,
                                           unsigned long long* grec, unsigned long long& cnt,
                                           const uint32_t* __restrict__ order) {
+    uint64_t cb = 0;  // first word of the triangle's cell record (F_MULTI)
+    uint32_t t1 = t.t_pq, t2 = t.t_pr, t3 = t.t_qr;
+    if (F & F_MULTI) {
+        sort3(t1, t2, t3);
+        const uint32_t* win = reinterpret_cast<const uint32_t*>(s_tab) - kMultiWords;
+        const uint32_t A = win[0], B = win[1];
+        const uint32_t* lo = win + 4;
+        const uint32_t* hi = win + 4 + kMultiMax;
+        uint32_t i = 0, j = 0;  // i: lower bounds <= t1; j: upper bounds < t3
+        for (uint32_t step = kMultiMax; step; step >>= 1) {
+            if (i + step <= A && lo[i + step - 1] <= t1) i += step;
+            if (j + step <= B && hi[j + step - 1] < t3) j += step;
+        }
+        if (i == 0 || j == B) keep = false;  // in no request's window
+        cb = ((uint64_t)(i - 1) * B + j) * a.lay.words;
+    }
     const unsigned km = __ballot_sync(0xffffffffu, keep);
     if (!km) return;
     if (!keep) return;
-    cnt += 1;
     const Layout& L = a.lay;
-    uint32_t t1 = t.t_pq, t2 = t.t_pr, t3 = t.t_qr;
-    if (F & F_TS) sort3(t1, t2, t3);
-    if (L.o_hist != ~0u) warp_add<F>(km, s_tab, a.s_words, grec, L.o_hist + time_bin(t3 - t1));
+    if (F & F_MULTI) {
+        if (L.o_count != ~0u) warp_add<F>(km, s_tab, a.s_words, grec, cb + L.o_count);
+    } else {
+        cnt += 1;
+        if (F & F_TS) sort3(t1, t2, t3);
+    }
+    if (L.o_hist != ~0u) warp_add<F>(km, s_tab, a.s_words, grec, cb + L.o_hist + time_bin(t3 - t1));
     if ((F & F_VL) && L.o_vtri != ~0u) {
         uint32_t x = t.l_p, y = t.l_q, z = t.l_r;
         sort3(x, y, z);
-        warp_add<F>(km, s_tab, a.s_words, grec, L.o_vtri + (x * a.Lv + y) * a.Lv + z);
+        warp_add<F>(km, s_tab, a.s_words, grec, cb + L.o_vtri + (x * a.Lv + y) * a.Lv + z);
     }
     if ((F & F_EL) && L.o_etri != ~0u) {
         uint32_t x = t.e_pq, y = t.e_pr, z = t.e_qr;
         sort3(x, y, z);
-        warp_add<F>(km, s_tab, a.s_words, grec, L.o_etri + (x * a.Le + y) * a.Le + z);
+        warp_add<F>(km, s_tab, a.s_words, grec, cb + L.o_etri + (x * a.Le + y) * a.Le + z);
     }
     if (F & F_EXTRA) {
         if (L.o_joint != ~0u)
-            rec_add<F>(s_tab, a.s_words, grec, L.o_joint + time_bin(t2 - t1) * TRIPOLL_HIST_BINS + time_bin(t3 - t1), 1);
+            rec_add<F>(s_tab, a.s_words, grec,
+                       cb + L.o_joint + time_bin(t2 - t1) * TRIPOLL_HIST_BINS + time_bin(t3 - t1), 1);
         if (L.o_maxel != ~0u && t.l_p != t.l_q && t.l_q != t.l_r && t.l_p != t.l_r)
-            rec_add<F>(s_tab, a.s_words, grec, L.o_maxel + max(t.e_pq, max(t.e_pr, t.e_qr)), 1);
+            rec_add<F>(s_tab, a.s_words, grec, cb + L.o_maxel + max(t.e_pq, max(t.e_pr, t.e_qr)), 1);
         if (L.o_degtri != ~0u) {
             uint32_t x = time_bin(t.d_p), y = time_bin(t.d_q), z = time_bin(t.d_r);
             sort3(x, y, z);
             rec_add<F>(s_tab, a.s_words, grec,
-                    L.o_degtri + (x * TRIPOLL_HIST_BINS + y) * TRIPOLL_HIST_BINS + z, 1);
+                       cb + L.o_degtri + (x * TRIPOLL_HIST_BINS + y) * TRIPOLL_HIST_BINS + z, 1);
         }
-        if (L.o_vlocal != ~0ull) {
-            atomicAdd(&grec[L.o_vlocal + order[t.p]], 1ull);
-            atomicAdd(&grec[L.o_vlocal + order[t.q]], 1ull);
-            atomicAdd(&grec[L.o_vlocal + order[t.r]], 1ull);
-        }
-        if (L.o_elocal != ~0ull) {
-            atomicAdd(&grec[L.o_elocal + t.x_pq], 1ull);
-            atomicAdd(&grec[L.o_elocal + t.x_pr], 1ull);
-            atomicAdd(&grec[L.o_elocal + t.x_qr], 1ull);
+        if (!(F & F_MULTI)) {  // local counts are never surveyed several windows at once
+            if (L.o_vlocal != ~0ull) {
+                atomicAdd(&grec[L.o_vlocal + order[t.p]], 1ull);
+                atomicAdd(&grec[L.o_vlocal + order[t.q]], 1ull);
+                atomicAdd(&grec[L.o_vlocal + order[t.r]], 1ull);
+            }
+            if (L.o_elocal != ~0ull) {
+                atomicAdd(&grec[L.o_elocal + t.x_pq], 1ull);
+                atomicAdd(&grec[L.o_elocal + t.x_pr], 1ull);
+                atomicAdd(&grec[L.o_elocal + t.x_qr], 1ull);
+            }
         }
     }
 }
@@ -661,9 +695,21 @@ __device__ void flush_shared(MirrorWord* s_tab, uint32_t s_words, unsigned long 
     }
 }
 
-// Clear the mirror (and the word cache) at kernel start.
+// Clear the mirror (and the word cache) at kernel start; load the requests' bounds (F_MULTI) from
+// the counters array: counters[4] = A, counters[5] = B, then the A lower and B upper bounds.
 template <int F>
-__device__ void init_shared(MirrorWord* s_tab, uint32_t s_words) {
+__device__ void init_shared(MirrorWord* s_tab, uint32_t s_words, const uint32_t* __restrict__ counters) {
+    if (F & F_MULTI) {
+        uint32_t* win = reinterpret_cast<uint32_t*>(s_tab) - kMultiWords;
+        const uint32_t A = counters[4], B = counters[5];
+        for (uint32_t i = threadIdx.x; i < kMultiWords; i += blockDim.x) {
+            uint32_t v = 0;
+            if (i < 2) v = counters[4 + i];
+            else if (i >= 4 && i < 4 + A) v = counters[6 + (i - 4)];
+            else if (i >= 4 + kMultiMax && i < 4 + kMultiMax + B) v = counters[6 + A + (i - 4 - kMultiMax)];
+            win[i] = v;
+        }
+    }
     for (uint32_t w = threadIdx.x; w < s_words; w += blockDim.x) s_tab[w] = 0;
     if (F & F_CACHE) {
         uint32_t* key = cache_keys(s_tab, s_words);
@@ -710,8 +756,8 @@ __global__ void __launch_bounds__(kBlockThreads, CHUNK <= kBlockChunk ? 5 : 3)
     __shared__ uint32_t scan_tmp[kWarps];
     __shared__ uint32_t s_item, s_total;
 
-    MirrorWord* s_tab = reinterpret_cast<MirrorWord*>(smem);
-    unsigned char* base = smem + mirror_bytes<F>(a.s_words);
+    MirrorWord* s_tab = reinterpret_cast<MirrorWord*>(smem + multi_bytes<F>());
+    unsigned char* base = smem + multi_bytes<F>() + mirror_bytes<F>(a.s_words);
     QTable<uint16_t> T;
     T.key = reinterpret_cast<uint32_t*>(base);
     T.ts = T.key + kBlockTable;
@@ -732,7 +778,7 @@ __global__ void __launch_bounds__(kBlockThreads, CHUNK <= kBlockChunk ? 5 : 3)
     T.el = reinterpret_cast<uint8_t*>(T.pos + kBlockTable);  // present only with F_EL
     T.vl = T.el + ((F & F_EL) ? CHUNK : 0);                  // present only with F_VL
 
-    init_shared<F>(s_tab, a.s_words);
+    init_shared<F>(s_tab, a.s_words, a.counters);
     unsigned long long cnt = 0;
     unsigned long long* grec_prev = nullptr;
     uint32_t taken = 0;  // items this block has taken (block-uniform)
@@ -816,11 +862,11 @@ template <int F>
 __global__ void __launch_bounds__(kBlockThreads, 5) survey_warp_kernel(GraphDev g, const WorkItem* __restrict__ items,
                                                                     uint32_t n_items, SurveyArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    MirrorWord* s_tab = reinterpret_cast<MirrorWord*>(smem);
-    WarpSmem* ws_all = reinterpret_cast<WarpSmem*>(smem + mirror_bytes<F>(a.s_words));
+    MirrorWord* s_tab = reinterpret_cast<MirrorWord*>(smem + multi_bytes<F>());
+    WarpSmem* ws_all = reinterpret_cast<WarpSmem*>(smem + multi_bytes<F>() + mirror_bytes<F>(a.s_words));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpSmem& ws = ws_all[warp];
-    init_shared<F>(s_tab, a.s_words);
+    init_shared<F>(s_tab, a.s_words, a.counters);
     __syncthreads();
     QTable<uint8_t> T;
     T.key = ws.key; T.pos = ws.pos; T.ts = ws.ts; T.deg = ws.deg; T.el = ws.el; T.vl = ws.vl;
@@ -907,7 +953,7 @@ void launch_f(const tripoll_graph* g, const GraphDev& gd, const SurveyArgs& a, c
               cudaEvent_t* ev) {
     mark(ev, 1, s);
     if (g->n_items_warp) {
-        size_t sm = mirror_bytes<F>(a.s_words) + kWarps * sizeof(WarpSmem);
+        size_t sm = multi_bytes<F>() + mirror_bytes<F>(a.s_words) + kWarps * sizeof(WarpSmem);
         const int per = blocks_per_sm((const void*)survey_warp_kernel<F>, sm);
         uint64_t blocks = (uint64_t)per * sms;
         blocks = std::min<uint64_t>(blocks, (g->n_items_warp + kWarps - 1) / kWarps);
@@ -916,7 +962,7 @@ void launch_f(const tripoll_graph* g, const GraphDev& gd, const SurveyArgs& a, c
     }
     mark(ev, 2, s);
     if (g->n_items_block) {
-        size_t sm = mirror_bytes<F>(a.s_words) + block_smem_fixed<F, kBlockChunk>();
+        size_t sm = multi_bytes<F>() + mirror_bytes<F>(a.s_words) + block_smem_fixed<F, kBlockChunk>();
         const int per = blocks_per_sm((const void*)survey_block_kernel<F, kBlockChunk, 1>, sm);
         uint64_t blocks = std::min<uint64_t>((uint64_t)per * sms, g->n_items_block);
         survey_block_kernel<F, kBlockChunk, 1><<<(unsigned)blocks, kBlockThreads, sm, s>>>(
@@ -924,7 +970,7 @@ void launch_f(const tripoll_graph* g, const GraphDev& gd, const SurveyArgs& a, c
     }
     mark(ev, 3, s);
     if (g->n_items_big) {
-        size_t sm = mirror_bytes<F>(a.s_words) + block_smem_fixed<F, kBigChunk>();
+        size_t sm = multi_bytes<F>() + mirror_bytes<F>(a.s_words) + block_smem_fixed<F, kBigChunk>();
         const int per = blocks_per_sm((const void*)survey_block_kernel<F, kBigChunk, 2>, sm);
         uint64_t blocks = std::min<uint64_t>((uint64_t)per * sms, g->n_items_big);
         survey_block_kernel<F, kBigChunk, 2><<<(unsigned)blocks, kBlockThreads, sm, s>>>(

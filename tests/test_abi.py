@@ -97,6 +97,7 @@ def test_invalid_arguments_are_rejected_before_any_gpu_work():
         "survey of no graph": lambda: tp.tripoll_survey(None, tp.TRIPOLL_COUNT, 0, 1, z),
         "pivot range of no graph": lambda: tp.tripoll_survey_range(None, tp.TRIPOLL_COUNT, 0, 1, 0, 1, z),
         "static survey of no graph": lambda: tp.tripoll_survey_static(None, tp.TRIPOLL_COUNT, 0, 1, z),
+        "several requests on no graph": lambda: tp.tripoll_survey_many(None, [tp.TRIPOLL_COUNT], [0], [1], [z]),
         "wedge checks of no graph": lambda: tp.tripoll_wedge_checks(None),
         "statistics of no graph": lambda: tp.tripoll_graph_stats(None),
         "partition of no graph": lambda: tp.tripoll_partition_pivots(None, 2),

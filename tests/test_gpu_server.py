@@ -152,3 +152,27 @@ def test_wait_times_out_and_the_request_stays_queued():
     finally:
         tp.tripoll_server_destroy(srv)
         tp.tripoll_destroy(h)
+
+
+def test_batches_without_room_for_the_union_window_view_match_the_oracle():
+    """A budget that holds several requests' cell records but not the union window's view: the server still
+    runs each graph's requests as one batch, skipping out-of-window edges in place; results equal the oracle."""
+    g = synth.rmat_graph(13, 16, 12, ts_bits=24, num_vlabels=16, num_elabels=8)
+    h = tp.tripoll_graph_create(g.src, g.dst, g.ts, g.elabel, g.vlabel, g.n, 16, 8)
+    srv = tp.tripoll_server_create(2 << 20, 64)  # 2 MB: records and results fit, a view of 130K edges does not
+    try:
+        slot = tp.tripoll_server_add_graph(srv, h)
+        reqs = []
+        for i in range(12):
+            d = [synth.draw(8, 1, 3 * i + j) for j in range(3)]
+            k = [tp.TRIPOLL_COUNT, tp.TRIPOLL_CLOSURE_HIST, tp.TRIPOLL_ELABEL_TRIPLES][d[0] % 3]
+            lo, hi = sorted(((d[1] >> 40) % (1 << 24), (d[2] >> 40) % (1 << 24)))
+            reqs.append((k, lo, hi, tp.tripoll_server_submit(srv, slot, k, lo, hi)))
+        for k, lo, hi, rid in reqs:
+            o = np.zeros(tp.tripoll_result_words(k, 16, 8, g.n), np.uint64)
+            tp.tripoll_server_wait(srv, rid, o, 120000)
+            want, _ = oracle_vector(g, k, window=(lo, hi))
+            assert np.array_equal(o, want), f"request {(k, lo, hi)} differs from the oracle"
+    finally:
+        tp.tripoll_server_destroy(srv)
+        tp.tripoll_destroy(h)
