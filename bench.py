@@ -149,6 +149,15 @@ def compulsory_bytes(st: dict) -> int:
     return 9 * st["num_vertices"] + (10 + 16) * st["num_edges"]
 
 
+def use_tuned_plan(tp, workload):
+    """Start new graphs with the plan the autotuner stored for this workload (tuned_plans.json), if any."""
+    from paper_2107_12330_b300 import tuning
+    plan = tuning.plan_for(workload)
+    tp.tripoll_set_default_plan(plan)
+    return {"plan": plan or dict(tp.DEFAULT_PLAN),
+            "plan_source": f"autotuned ({workload}, tuned_plans.json v{tuning.FORMAT_VERSION})" if plan else "defaults"}
+
+
 def run_tripoll(args):
     import torch
     import torch.distributed as dist
@@ -176,6 +185,7 @@ def run_tripoll(args):
     words = tp.tripoll_result_words(kinds, g.num_vlabels, g.num_elabels, g.n)
     result = torch.zeros(words, dtype=torch.int64, device=dev)
     stream = torch.cuda.current_stream(dev)
+    plan = use_tuned_plan(tp, f"rmat{args.scale}")
 
     def build():
         return tp.tripoll_graph_create(src, dst, ts, el, vl, g.n, g.num_vlabels, g.num_elabels, stream=stream)
@@ -288,7 +298,7 @@ def run_tripoll(args):
                    "step": "build G+ from device-resident edge arrays + survey + release",
                    "input_edges": m_in, "edges": info["num_edges"], "wedges": info["wedges"], "wedge_checks_in_window": wedge_checks,
                    "triangles_in_window": triangles, "l2": l2_note,
-                   "parallelism": f"pivot shards x{world}"},
+                   "parallelism": f"pivot shards x{world}", **plan},
         "survey_ms": survey_avg, "survey_ms_p50": survey_med, "survey_ms_p99": survey_p99,
         "survey_latency": {"p50_ms": survey_med, "p99_ms": survey_p99, "over": f"{args.steps} timed surveys"},
         "survey_phases_ms": {"window_view": ph[0], "survey_warp_kernel": ph[1], "survey_block_kernel": ph[2],
@@ -448,6 +458,7 @@ def run_batched(args):
     w = tp.tripoll_result_words(kinds, 4, 1, 0)
     result = torch.zeros(w * G, dtype=torch.int64, device=dev)
     stream = torch.cuda.current_stream(dev)
+    plan = use_tuned_plan(tp, f"batched{G}")
 
     def build():
         return tp.tripoll_batch_create(d["src"], d["dst"], d["ts"], None, eoff, d["vlabel"], nv, 4, 0, stream=stream)
@@ -526,7 +537,7 @@ def run_batched(args):
                                "uniform [4,64], seeds 0..; ts uniform [0,2^20), vlabel 4; per-graph count + "
                                "closure histogram", "input_edges": int(eoff[-1]), "edges": info["num_edges"],
                    "wedges": info["wedges"], "triangles": triangles,
-                   "step": "batched build + one survey launch pair + release"},
+                   "step": "batched build + one survey launch pair + release", **plan},
         "triangles_per_s": triangles / (ms * 1e-3), "survey_ms": survey_ms, "build_ms": ms - survey_ms,
         "survey_graphs_per_s": batched_graphs_per_s,
         "plain_path": {"graphs": P, "survey_graphs_per_s": plain_graphs_per_s,

@@ -118,6 +118,28 @@ typedef struct {
     uint64_t device_bytes;   /* HBM held by the graph */
 } tripoll_graph_info;
 
+/* The survey plan of a graph: how middle vertices q are split into work items
+ * (the load balancing of the wedge checks; the paper's Sec. 4.2 notes hub
+ * imbalance, which the degree order only partly removes) and how a window is
+ * applied.  Results never depend on it; speed does, by workload.
+ *   warp_max_dplus       out-lists up to this length are surveyed one item per
+ *                        warp (32..256; larger ones one item per block).
+ *   block_item_in_edges  in-edges (p,q) per block item (256..2048, a multiple
+ *                        of 256).
+ *   long_list_min_dplus  out-lists longer than this go to the long-list kernel
+ *                        (2048-entry parts; 1024..65536).
+ *   window_view          1: a window compacts G+ to its in-window edges first
+ *                        (tripoll_survey); 0: out-of-window edges are skipped
+ *                        where they are met (no extra memory).
+ * The bounds keep every on-chip partial sum below 2^32.  Defaults: 128, 2048,
+ * 4096, 1. */
+typedef struct {
+    uint32_t warp_max_dplus;
+    uint32_t block_item_in_edges;
+    uint32_t long_list_min_dplus;
+    uint32_t window_view;
+} tripoll_plan;
+
 /* Build G+ on the device (Sec. 3, Sec. 4.2): drop records with src == dst; merge
  * all records of an unordered pair into one edge keeping the lexicographic
  * minimum (timestamp, then edge label) -- the chronologically first record of
@@ -241,6 +263,32 @@ int tripoll_survey_timed(tripoll_graph_t g, uint32_t kind_mask, uint32_t t_lo, u
  *     result. */
 int tripoll_survey_static(tripoll_graph_t g, uint32_t kind_mask, uint32_t t_lo, uint32_t t_hi,
                           uint64_t* result, void* cuda_stream);
+
+/* The plan of g (*plan: host).  Errors: INVALID_ARG for NULL arguments. */
+int tripoll_get_plan(tripoll_graph_t g, tripoll_plan* plan);
+
+/* Give g another plan: its work items are rebuilt on cuda_stream (a few
+ * kernels over the vertices; no survey may run on g meanwhile).  Errors:
+ * INVALID_ARG for a plan outside the bounds above, NO_MEMORY, CUDA.
+ * Synchronises cuda_stream. */
+int tripoll_set_plan(tripoll_graph_t g, const tripoll_plan* plan, void* cuda_stream);
+
+/* The plan graphs built from now on start with (process-wide; NULL restores
+ * the defaults).  Errors: INVALID_ARG for a plan outside the bounds. */
+int tripoll_set_default_plan(const tripoll_plan* plan);
+
+/* The autotuner: time surveys of g (kinds, window) under candidate plans and
+ * keep the fastest.  Coordinate descent from g's current plan: each field in
+ * turn takes each of its candidate values (warp_max_dplus 32, 64, 128, 256;
+ * block_item_in_edges 512, 1024, 2048; long_list_min_dplus 2048, 4096, 8192;
+ * window_view 1, 0 when the window is not the full range) with the others
+ * fixed; a plan's time is the median of `reps` surveys (device time, CUDA
+ * events on cuda_stream, after one untimed survey).  g ends with the best plan,
+ * which *best (host) receives with its time *best_ms and the starting plan's
+ * time *start_ms (both host, may be NULL).  Errors: those of tripoll_survey
+ * and tripoll_set_plan.  Synchronises cuda_stream. */
+int tripoll_tune(tripoll_graph_t g, uint32_t kind_mask, uint32_t t_lo, uint32_t t_hi, uint32_t reps,
+                 tripoll_plan* best, float* best_ms, float* start_ms, void* cuda_stream);
 
 /* Split [0, n) into `parts` pivot ranges of near-equal survey cost (the
  * out-list entries each pivot's wedge checks read).  bounds: host,

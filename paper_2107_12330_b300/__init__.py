@@ -46,7 +46,8 @@ EXPORTS = (
     "tripoll_destroy", "tripoll_server_create", "tripoll_server_add_graph", "tripoll_server_submit",
     "tripoll_server_wait", "tripoll_server_destroy", "tripoll_status_string", "tripoll_last_error",
     "tripoll_launch_count", "tripoll_wedge_checks", "tripoll_survey_static", "tripoll_set_allocator",
-    "tripoll_survey_timed", "tripoll_survey_many", "tripoll_server_stats",
+    "tripoll_survey_timed", "tripoll_survey_many", "tripoll_server_stats", "tripoll_get_plan",
+    "tripoll_set_plan", "tripoll_set_default_plan", "tripoll_tune",
 )
 
 # C signatures of the allocator hook (tripoll_alloc_fn, tripoll_free_fn)
@@ -72,6 +73,21 @@ class GraphInfo(ctypes.Structure):
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
+
+class Plan(ctypes.Structure):
+    """tripoll_plan: the survey plan of a graph (see tripoll.h)."""
+    _fields_ = [("warp_max_dplus", ctypes.c_uint32), ("block_item_in_edges", ctypes.c_uint32),
+                ("long_list_min_dplus", ctypes.c_uint32), ("window_view", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+    @classmethod
+    def of(cls, d):
+        return d if isinstance(d, cls) else cls(**{k: int(d[k]) for k, _ in cls._fields_})
+
+
+DEFAULT_PLAN = {"warp_max_dplus": 128, "block_item_in_edges": 2048, "long_list_min_dplus": 4096, "window_view": 1}
 
 _lib = None
 
@@ -113,13 +129,20 @@ def load_library(path: str = LIB_PATH):
     lib.tripoll_survey_timed.argtypes = [vp, u32, u32, u32, u64, u64, vp, vp, vp]
     lib.tripoll_survey_many.argtypes = [vp, u32, vp, vp, vp, vp, vp]
     lib.tripoll_server_stats.argtypes = [vp, vp]
+    pplan = ctypes.POINTER(Plan)
+    lib.tripoll_get_plan.argtypes = [vp, pplan]
+    lib.tripoll_set_plan.argtypes = [vp, pplan, vp]
+    lib.tripoll_set_default_plan.argtypes = [pplan]
+    lib.tripoll_tune.argtypes = [vp, u32, u32, u32, u32, pplan, ctypes.POINTER(ctypes.c_float),
+                                 ctypes.POINTER(ctypes.c_float), vp]
     lib.tripoll_launch_count.argtypes = []
     lib.tripoll_launch_count.restype = u64
     for name in ("tripoll_graph_create", "tripoll_batch_create", "tripoll_survey", "tripoll_survey_range",
                  "tripoll_partition_pivots", "tripoll_graph_stats", "tripoll_graph_export",
                  "tripoll_server_create", "tripoll_server_add_graph", "tripoll_server_submit",
                  "tripoll_server_wait", "tripoll_wedge_checks", "tripoll_survey_static", "tripoll_set_allocator",
-                 "tripoll_survey_timed", "tripoll_survey_many", "tripoll_server_stats"):
+                 "tripoll_survey_timed", "tripoll_survey_many", "tripoll_server_stats", "tripoll_get_plan",
+                 "tripoll_set_plan", "tripoll_set_default_plan", "tripoll_tune"):
         getattr(lib, name).restype = i32
     _lib = lib
     return lib
@@ -244,6 +267,32 @@ def tripoll_survey_timed(g, kind_mask, t_lo, t_hi, pivot_lo, pivot_hi, result, s
     _check(load_library().tripoll_survey_timed(g, kind_mask, t_lo, t_hi, pivot_lo, pivot_hi, _ptr(result), ms,
                                                _stream(stream)), "tripoll_survey_timed")
     return [float(x) for x in ms]
+
+
+def tripoll_get_plan(g):
+    p = Plan()
+    _check(load_library().tripoll_get_plan(g, ctypes.byref(p)), "tripoll_get_plan")
+    return p.as_dict()
+
+
+def tripoll_set_plan(g, plan, stream=None):
+    p = Plan.of(plan)
+    _check(load_library().tripoll_set_plan(g, ctypes.byref(p), _stream(stream)), "tripoll_set_plan")
+
+
+def tripoll_set_default_plan(plan=None):
+    """The plan graphs built from now on start with (None: the built-in defaults)."""
+    p = None if plan is None else ctypes.byref(Plan.of(plan))
+    _check(load_library().tripoll_set_default_plan(p), "tripoll_set_default_plan")
+
+
+def tripoll_tune(g, kind_mask, t_lo=0, t_hi=0xFFFFFFFF, reps=3, stream=None):
+    """Autotune g's plan for this survey; returns (best plan dict, its ms, the starting plan's ms)."""
+    p = Plan()
+    best, start = ctypes.c_float(), ctypes.c_float()
+    _check(load_library().tripoll_tune(g, kind_mask, t_lo, t_hi, reps, ctypes.byref(p), ctypes.byref(best),
+                                       ctypes.byref(start), _stream(stream)), "tripoll_tune")
+    return p.as_dict(), float(best.value), float(start.value)
 
 
 def tripoll_partition_pivots(g, parts, stream=None):

@@ -99,6 +99,38 @@ void dev_free(void* p, size_t bytes, cudaStream_t s, const Allocator& a) {
     else cudaFreeAsync(p, s);
 }
 
+void drop_block(tripoll_graph* g, void* ptr, cudaStream_t s) {
+    for (size_t i = 0; i < g->blocks.size(); ++i)
+        if (g->blocks[i].ptr == ptr) {
+            dev_free(ptr, g->blocks[i].bytes, s, g->blocks[i].al);
+            g->blocks.erase(g->blocks.begin() + i);
+            return;
+        }
+}
+
+// ---- survey plans ------------------------------------------------------------------------------
+
+namespace {
+std::mutex g_plan_mu;
+tripoll_plan g_default_plan = {kWarpPlanQ, kItemInEdges, 4 * kBlockChunk, 1};
+}  // namespace
+
+tripoll_plan default_plan() {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    return g_default_plan;
+}
+
+int check_plan(const tripoll_plan& p) {
+    if (p.warp_max_dplus < 32 || p.warp_max_dplus > kWarpPlanMax)
+        return fail(TRIPOLL_ERR_INVALID_ARG, "warp_max_dplus must lie in 32..256");
+    if (p.block_item_in_edges < 256 || p.block_item_in_edges > kItemInEdges || p.block_item_in_edges % 256)
+        return fail(TRIPOLL_ERR_INVALID_ARG, "block_item_in_edges must be a multiple of 256 in 256..2048");
+    if (p.long_list_min_dplus < kBlockChunk || p.long_list_min_dplus > 65536)
+        return fail(TRIPOLL_ERR_INVALID_ARG, "long_list_min_dplus must lie in 1024..65536");
+    if (p.window_view > 1) return fail(TRIPOLL_ERR_INVALID_ARG, "window_view must be 0 or 1");
+    return TRIPOLL_OK;
+}
+
 void swap_block(tripoll_graph* g, void* graph_ptr, Scratch& sc) {
     for (Block& b : g->blocks)
         if (b.ptr == graph_ptr) {
@@ -156,7 +188,8 @@ int survey_into(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_t 
     }
     TP_CUDA(cudaMemsetAsync(a, 0, words * 8, s));
     if (p_hi > g->n) p_hi = g->n;
-    if (p_lo < p_hi && (rc = launch_survey(g, kinds, t_lo, t_hi, p_lo, p_hi, a, ctr.as<uint32_t>(), s, true, ev)))
+    if (p_lo < p_hi &&
+        (rc = launch_survey(g, kinds, t_lo, t_hi, p_lo, p_hi, a, ctr.as<uint32_t>(), s, g->plan.window_view != 0, ev)))
         return rc;
     if (!dev_result) {
         TP_CUDA(cudaMemcpyAsync(result, a, words * 8, cudaMemcpyDeviceToHost, s));
@@ -295,6 +328,106 @@ extern "C" int tripoll_survey_timed(tripoll_graph_t g, uint32_t kind_mask, uint3
     if ((rc = survey_into(g, kind_mask, t_lo, t_hi, pivot_lo, pivot_hi, result, s, ev))) return rc;
     TP_CUDA(cudaStreamSynchronize(s));
     for (int k = 0; k < 4; ++k) TP_CUDA(cudaEventElapsedTime(&phase_ms[k], ev[k], ev[k + 1]));
+    return TRIPOLL_OK;
+}
+
+extern "C" int tripoll_get_plan(tripoll_graph_t g, tripoll_plan* plan) {
+    if (!g || !plan) return fail(TRIPOLL_ERR_INVALID_ARG, "NULL argument");
+    *plan = g->plan;
+    return TRIPOLL_OK;
+}
+
+static bool same_items(const tripoll_plan& a, const tripoll_plan& b) {
+    return a.warp_max_dplus == b.warp_max_dplus && a.block_item_in_edges == b.block_item_in_edges &&
+           a.long_list_min_dplus == b.long_list_min_dplus;
+}
+
+extern "C" int tripoll_set_plan(tripoll_graph_t g, const tripoll_plan* plan, void* cuda_stream) {
+    if (!g || !plan) return fail(TRIPOLL_ERR_INVALID_ARG, "NULL argument");
+    int rc = check_plan(*plan);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const bool rebuild = !same_items(g->plan, *plan);
+    g->plan = *plan;
+    if (rebuild && (rc = build_plan(g, s))) return rc;
+    TP_CUDA(cudaStreamSynchronize(s));
+    return TRIPOLL_OK;
+}
+
+extern "C" int tripoll_set_default_plan(const tripoll_plan* plan) {
+    tripoll_plan p = {kWarpPlanQ, kItemInEdges, 4 * kBlockChunk, 1};
+    if (plan) {
+        int rc = check_plan(*plan);
+        if (rc) return rc;
+        p = *plan;
+    }
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    g_default_plan = p;
+    return TRIPOLL_OK;
+}
+
+extern "C" int tripoll_tune(tripoll_graph_t g, uint32_t kind_mask, uint32_t t_lo, uint32_t t_hi, uint32_t reps,
+                            tripoll_plan* best, float* best_ms, float* start_ms, void* cuda_stream) {
+    int rc = check_survey_args(g, kind_mask, t_lo, t_hi, &kind_mask);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    reps = std::max(1u, reps);
+    const uint64_t words = make_layout(kind_mask, g->Lv, g->Le, g->n, g->m).words * g->num_graphs;
+    Scratch res;
+    TP_CUDA(res.alloc(words * 8, s));
+    cudaEvent_t e0, e1;
+    TP_CUDA(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(TRIPOLL_ERR_CUDA, "cudaEventCreate");
+    }
+    struct Events {
+        cudaEvent_t a, b;
+        ~Events() { cudaEventDestroy(a); cudaEventDestroy(b); }
+    } guard{e0, e1};
+    // median device time of `reps` surveys under plan P (g keeps P)
+    auto time_plan = [&](const tripoll_plan& P, float* ms) -> int {
+        int r = tripoll_set_plan(g, &P, s);
+        if (r) return r;
+        if ((r = survey_into(g, kind_mask, t_lo, t_hi, 0, g->n, res.as<uint64_t>(), s))) return r;
+        std::vector<float> t;
+        for (uint32_t k = 0; k < reps; ++k) {
+            TP_CUDA(cudaEventRecord(e0, s));
+            if ((r = survey_into(g, kind_mask, t_lo, t_hi, 0, g->n, res.as<uint64_t>(), s))) return r;
+            TP_CUDA(cudaEventRecord(e1, s));
+            TP_CUDA(cudaEventSynchronize(e1));
+            float x = 0;
+            TP_CUDA(cudaEventElapsedTime(&x, e0, e1));
+            t.push_back(x);
+        }
+        std::sort(t.begin(), t.end());
+        *ms = t[t.size() / 2];
+        return TRIPOLL_OK;
+    };
+    tripoll_plan cur = g->plan;
+    float cur_ms = 0;
+    if ((rc = time_plan(cur, &cur_ms))) return rc;
+    if (start_ms) *start_ms = cur_ms;
+    const bool window = !(t_lo == 0 && t_hi == 0xFFFFFFFFu);
+    const std::vector<uint32_t> cand[4] = {{32, 64, 128, 256}, {512, 1024, 2048}, {2048, 4096, 8192},
+                                           window ? std::vector<uint32_t>{1, 0} : std::vector<uint32_t>{}};
+    for (int f = 0; f < 4; ++f) {
+        for (uint32_t v : cand[f]) {
+            tripoll_plan P = cur;
+            uint32_t* field[4] = {&P.warp_max_dplus, &P.block_item_in_edges, &P.long_list_min_dplus, &P.window_view};
+            if (*field[f] == v) continue;
+            *field[f] = v;
+            float ms = 0;
+            if ((rc = time_plan(P, &ms))) return rc;
+            if (ms < cur_ms) {
+                cur = P;
+                cur_ms = ms;
+            }
+        }
+    }
+    if ((rc = tripoll_set_plan(g, &cur, s))) return rc;
+    if (best) *best = cur;
+    if (best_ms) *best_ms = cur_ms;
     return TRIPOLL_OK;
 }
 

@@ -406,6 +406,7 @@ int build_impl(const uint32_t* src_h, const uint32_t* dst_h, const uint32_t* ts_
     g->Lv = Lv;
     g->Le = el_h ? Le : 1;
     g->has_el = el_h != nullptr;
+    g->plan = default_plan();
 
     // 2. canonical keys + payloads, sort, keep min payload per key run
     uint32_t* fault = flags_d.as<uint32_t>() + 1;  // look-back waits of the radix sorts that gave up

@@ -153,10 +153,11 @@ struct tripoll_graph {
     uint32_t* graph_of = nullptr;
     uint64_t* in_off = nullptr;
     tp::InEdge* in_edge = nullptr;
-    // survey plan
-    tp::WorkItem* items_warp = nullptr;   // d+(q) <= kWarpPlanQ
-    tp::WorkItem* items_block = nullptr;  // kWarpPlanQ < d+(q) <= 4 kBlockChunk
-    tp::WorkItem* items_big = nullptr;    // d+(q) > kBlockChunk, chunks of kBigChunk
+    // survey plan (the thresholds of plan; see tripoll_plan)
+    tripoll_plan plan{};
+    tp::WorkItem* items_warp = nullptr;   // d+(q) <= plan.warp_max_dplus
+    tp::WorkItem* items_block = nullptr;  // up to plan.long_list_min_dplus, parts of kBlockChunk
+    tp::WorkItem* items_big = nullptr;    // longer out-lists, parts of kBigChunk
     uint64_t n_items_warp = 0, n_items_block = 0, n_items_big = 0;
     // statistics
     tripoll_graph_info info{};
@@ -182,7 +183,12 @@ constexpr uint32_t kBlockChunk = 1024;  // on-chip staged entries of q's out-lis
 constexpr uint32_t kBigChunk = 2048;    // the same for the large-table block kernel
 constexpr uint32_t kWarpInEdges = 64;   // in-edges per warp item
 constexpr uint32_t kBlockInEdges = 256; // in-edges a block stages at a time
-constexpr uint32_t kItemInEdges = 2048; // in-edges per block item (staged kBlockInEdges at a time)
+constexpr uint32_t kItemInEdges = 2048; // in-edges per block item (staged kBlockInEdges at a time): the default
+                                        // and the largest value the 32-bit on-chip sums allow
+constexpr uint32_t kWarpPlanMax = 256;  // largest warp-item out-list the warp kernel's 32-bit sums allow
+// The plan new graphs get (tripoll_set_default_plan), and the check of a plan's bounds.
+tripoll_plan default_plan();
+int check_plan(const tripoll_plan& p);
 constexpr uint32_t kColPad = 8;         // col[] entries past m (0xFFFFFFFF) for 32-byte vector loads
 
 // layout of one survey result record, in words (absent tables: ~0)
@@ -194,7 +200,10 @@ struct Layout {
 };
 Layout make_layout(uint32_t kinds, uint32_t Lv, uint32_t Le, uint64_t n, uint64_t m);
 
+// (Re)build g's work items under g->plan; items of an earlier plan are released.
 int build_plan(tripoll_graph* g, cudaStream_t s);
+// Return one of g's arrays to its allocator (stream-ordered on s) and forget it.
+void drop_block(tripoll_graph* g, void* ptr, cudaStream_t s);
 // Launch the survey kernels accumulating into `acc` (zeroed by the caller);
 // counters: device uint32[4] of scratch.  With window_view, a window that is
 // not [0, 0xFFFFFFFF] first compacts G+ to its in-window edges in pool memory

@@ -90,21 +90,22 @@ __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < 
 
 // Items of middle vertex q: for each part of Adj+(q) staged at once (one part
 // unless d+(q) exceeds the kernel's chunk), groups of at most `per` in-edges.
-__device__ __forceinline__ void plan_shape(uint64_t dp, uint64_t di, int& kind, uint64_t& chunk, uint64_t& per) {
-    kind = dp <= kWarpPlanQ ? 0 : (dp <= 4 * kBlockChunk ? 1 : 2);
-    chunk = kind == 0 ? kWarpPlanQ : (kind == 1 ? kBlockChunk : kBigChunk);
-    per = kind == 0 ? kWarpInEdges : kItemInEdges;
+__device__ __forceinline__ void plan_shape(uint64_t dp, uint64_t di, const tripoll_plan& P, int& kind, uint64_t& chunk,
+                                           uint64_t& per) {
+    kind = dp <= P.warp_max_dplus ? 0 : (dp <= P.long_list_min_dplus ? 1 : 2);
+    chunk = kind == 0 ? P.warp_max_dplus : (kind == 1 ? kBlockChunk : kBigChunk);
+    per = kind == 0 ? kWarpInEdges : P.block_item_in_edges;
 }
 
 __global__ void plan_count_kernel(const uint64_t* __restrict__ off, const uint64_t* __restrict__ in_off, uint64_t n,
-                                  uint32_t* __restrict__ c0, uint32_t* __restrict__ c1, uint32_t* __restrict__ c2) {
+                                  tripoll_plan P, uint32_t* __restrict__ c0, uint32_t* __restrict__ c1, uint32_t* __restrict__ c2) {
     for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < n; q += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t dp = off[q + 1] - off[q], di = in_off[q + 1] - in_off[q];
         uint32_t cnt[3] = {0, 0, 0};
         if (dp > 0 && di > 0) {
             int kind;
             uint64_t chunk, per;
-            plan_shape(dp, di, kind, chunk, per);
+            plan_shape(dp, di, P, kind, chunk, per);
             cnt[kind] = (uint32_t)(((dp + chunk - 1) / chunk) * ((di + per - 1) / per));
         }
         c0[q] = cnt[0];
@@ -114,7 +115,7 @@ __global__ void plan_count_kernel(const uint64_t* __restrict__ off, const uint64
 }
 
 __global__ void plan_fill_kernel(const uint64_t* __restrict__ off, const uint64_t* __restrict__ in_off, uint64_t n,
-                                 const uint32_t* __restrict__ o0, const uint32_t* __restrict__ o1,
+                                 tripoll_plan P, const uint32_t* __restrict__ o0, const uint32_t* __restrict__ o1,
                                  const uint32_t* __restrict__ o2, WorkItem* __restrict__ i0, WorkItem* __restrict__ i1,
                                  WorkItem* __restrict__ i2) {
     for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < n; q += (uint64_t)gridDim.x * blockDim.x) {
@@ -122,7 +123,7 @@ __global__ void plan_fill_kernel(const uint64_t* __restrict__ off, const uint64_
         if (dp == 0 || di == 0) continue;
         int kind;
         uint64_t chunk, per;
-        plan_shape(dp, di, kind, chunk, per);
+        plan_shape(dp, di, P, kind, chunk, per);
         WorkItem* dst = kind == 0 ? i0 : (kind == 1 ? i1 : i2);
         uint32_t o = kind == 0 ? o0[q] : (kind == 1 ? o1[q] : o2[q]);
         const uint32_t ilo = (uint32_t)in_off[q];
@@ -250,7 +251,7 @@ int build_plan(tripoll_graph* g, cudaStream_t s) {
         TP_CUDA(cudaMemsetAsync(c[k].ptr, 0, (n + 1) * 4, s));
     }
     if (n)
-        plan_count_kernel<<<grid_n(n), 256, 0, s>>>(g->off, g->in_off, n, c[0].as<uint32_t>(), c[1].as<uint32_t>(),
+        plan_count_kernel<<<grid_n(n), 256, 0, s>>>(g->off, g->in_off, n, g->plan, c[0].as<uint32_t>(), c[1].as<uint32_t>(),
                                                     c[2].as<uint32_t>()); ::tp::note_launch();
     TP_CUDA(cudaGetLastError());
     TP_CUDA(tmp.alloc(prim::scan_scratch_bytes(n + 1), s));
@@ -263,6 +264,10 @@ int build_plan(tripoll_graph* g, cudaStream_t s) {
         TP_CUDA(cudaMemcpyAsync(&tot[k], o[k].as<uint32_t>() + n, 4, cudaMemcpyDeviceToHost, s));
     }
     TP_CUDA(cudaStreamSynchronize(s));
+    for (WorkItem** items : {&g->items_warp, &g->items_block, &g->items_big}) {  // an earlier plan's items
+        if (*items) drop_block(g, *items, s);
+        *items = nullptr;
+    }
     g->n_items_warp = tot[0];
     g->n_items_block = tot[1];
     g->n_items_big = tot[2];
@@ -270,7 +275,7 @@ int build_plan(tripoll_graph* g, cudaStream_t s) {
     TP_CUDA(galloc(g, &g->items_block, std::max<uint64_t>(1, tot[1]), s));
     TP_CUDA(galloc(g, &g->items_big, std::max<uint64_t>(1, tot[2]), s));
     if (n)
-        plan_fill_kernel<<<grid_n(n), 256, 0, s>>>(g->off, g->in_off, n, o[0].as<uint32_t>(), o[1].as<uint32_t>(),
+        plan_fill_kernel<<<grid_n(n), 256, 0, s>>>(g->off, g->in_off, n, g->plan, o[0].as<uint32_t>(), o[1].as<uint32_t>(),
                                                    o[2].as<uint32_t>(), g->items_warp, g->items_block,
                                                    g->items_big); ::tp::note_launch();
     TP_CUDA(cudaGetLastError());
@@ -513,5 +518,6 @@ int survey_many(const tripoll_graph* g, uint32_t count, const uint32_t* kinds, c
 
 extern "C" int tripoll_survey_many(tripoll_graph_t g, uint32_t count, const uint32_t* kind_masks, const uint32_t* t_lo,
                                    const uint32_t* t_hi, uint64_t* const* results, void* cuda_stream) {
-    return tp::survey_many(g, count, kind_masks, t_lo, t_hi, results, (cudaStream_t)cuda_stream, true);
+    return tp::survey_many(g, count, kind_masks, t_lo, t_hi, results, (cudaStream_t)cuda_stream,
+                           !g || g->plan.window_view != 0);
 }

@@ -121,3 +121,33 @@ def test_allocator_hook_installs_and_restores_on_the_host():
         assert calls == []
     finally:
         tp.tripoll_set_allocator(None, None)
+
+
+def test_plans_outside_their_bounds_are_rejected_on_the_host():
+    """The plan bounds keep every on-chip 32-bit partial sum below 2^32: plans outside them are refused."""
+    good = dict(tp.DEFAULT_PLAN)
+    bad = [("warp_max_dplus", 16), ("warp_max_dplus", 512), ("block_item_in_edges", 300),
+           ("block_item_in_edges", 4096), ("long_list_min_dplus", 512), ("long_list_min_dplus", 1 << 17),
+           ("window_view", 2)]
+    for field, value in bad:
+        p = dict(good, **{field: value})
+        with pytest.raises(tp.TripollError) as e:
+            tp.tripoll_set_default_plan(p)
+        assert e.value.status == tp.TRIPOLL_ERR_INVALID_ARG, (field, value)
+    tp.tripoll_set_default_plan(dict(good, warp_max_dplus=256, block_item_in_edges=256))
+    tp.tripoll_set_default_plan(None)
+
+
+def test_tuned_plan_file_round_trip(tmp_path):
+    from paper_2107_12330_b300 import tuning
+    path = str(tmp_path / "plans.json")
+    assert tuning.plan_for("rmat24", path) is None
+    tuning.store_plan("rmat24", {"plan": dict(tp.DEFAULT_PLAN, warp_max_dplus=64), "survey_ms": 1.0}, path)
+    assert tuning.plan_for("rmat24", path)["warp_max_dplus"] == 64
+    import json
+    with open(path) as f:
+        data = json.load(f)
+    data["version"] = tuning.FORMAT_VERSION + 1
+    with open(path, "w") as f:
+        json.dump(data, f)
+    assert tuning.plan_for("rmat24", path) is None  # another format version is ignored
