@@ -98,10 +98,13 @@ __global__ void validate_vl_kernel(const uint8_t* __restrict__ vl, uint64_t n, u
     if (f) atomicOr(flags, f);
 }
 
+// Records of the sorts: the pair key in the low 2b bits of a 64-bit word and the payload
+// (ts << 8 | elabel) split between the word and a value of type V (prim::rec_word).
+template <class V>
 __global__ void canon_kernel(const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst,
                              const uint32_t* __restrict__ ts, const uint8_t* __restrict__ el, uint64_t m,
                              const uint64_t* __restrict__ eoff, const uint64_t* __restrict__ vbase, uint32_t G,
-                             int b, uint64_t sentinel, uint64_t* __restrict__ key, uint64_t* __restrict__ val) {
+                             int b, uint64_t sentinel, uint64_t* __restrict__ key, V* __restrict__ val) {
     uint64_t lo, hi;
     block_records(m, lo, hi);
     GraphCursor gc(eoff, G, lo + threadIdx.x);
@@ -113,8 +116,9 @@ __global__ void canon_kernel(const uint32_t* __restrict__ src, const uint32_t* _
             v += base;
         }
         uint64_t lo = u < v ? u : v, hi = u < v ? v : u;
-        key[i] = (u == v) ? sentinel : ((lo << b) | hi);
-        val[i] = ((uint64_t)ts[i] << 8) | (el ? el[i] : 0u);
+        const uint64_t payload = ((uint64_t)ts[i] << 8) | (el ? el[i] : 0u);
+        key[i] = prim::rec_word<V>((u == v) ? sentinel : ((lo << b) | hi), payload, 2 * b);
+        val[i] = (V)payload;
     }
 }
 
@@ -184,29 +188,32 @@ __global__ void rank_kernel(const uint64_t* __restrict__ vkey, uint64_t n, int b
     }
 }
 
-__global__ void orient_kernel(const uint64_t* __restrict__ ukey, uint64_t m, int b, const uint32_t* __restrict__ rank,
-                              uint64_t* __restrict__ okey) {
+template <class V>
+__global__ void orient_kernel(const uint64_t* __restrict__ ukey, const uint64_t* __restrict__ uval, uint64_t m, int b,
+                              const uint32_t* __restrict__ rank, uint64_t* __restrict__ okey, V* __restrict__ oval) {
     const uint64_t mask = (1ull << b) - 1;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m;
          i += (uint64_t)gridDim.x * blockDim.x) {
         uint64_t k = ukey[i];
         uint64_t ru = rank[k >> b], rv = rank[k & mask];
         uint64_t s = ru < rv ? ru : rv, d = ru < rv ? rv : ru;
-        okey[i] = (s << b) | d;
+        const uint64_t payload = uval[i];
+        okey[i] = prim::rec_word<V>((s << b) | d, payload, 2 * b);
+        oval[i] = (V)payload;
     }
 }
 
-// Runs of equal (key >> shift) in keys sorted ascending: first[v] and last[v]
+// Runs of equal ((key & kmask) >> shift) in keys sorted ascending: first[v] and last[v]
 // get the run of value v as [first, last) (both left 0 for absent values), so
 // that last - first counts the keys of v without atomics.
 template <class K>
-__global__ void run_ends_kernel(const K* __restrict__ key, uint64_t m, int shift, uint32_t* __restrict__ first,
-                                uint32_t* __restrict__ last) {
+__global__ void run_ends_kernel(const K* __restrict__ key, uint64_t m, uint64_t kmask, int shift,
+                                uint32_t* __restrict__ first, uint32_t* __restrict__ last) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m;
          i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t v = (uint64_t)(key[i] >> shift);
-        if (i == 0 || (uint64_t)(key[i - 1] >> shift) != v) first[v] = (uint32_t)i;
-        if (i + 1 == m || (uint64_t)(key[i + 1] >> shift) != v) last[v] = (uint32_t)(i + 1);
+        const uint64_t v = ((uint64_t)key[i] & kmask) >> shift;
+        if (i == 0 || (((uint64_t)key[i - 1] & kmask) >> shift) != v) first[v] = (uint32_t)i;
+        if (i + 1 == m || (((uint64_t)key[i + 1] & kmask) >> shift) != v) last[v] = (uint32_t)(i + 1);
     }
 }
 
@@ -218,14 +225,16 @@ __global__ void run_count_kernel(const uint32_t* __restrict__ first, uint32_t* _
 // CSR arrays of G+ from the (source, target)-sorted edges, plus, in the same
 // order, the in-edge record of every edge and the key of the in-edge order
 // (the target alone: a stable sort on it keeps sources ascending).
-__global__ void csr_fill_kernel(const uint64_t* __restrict__ okey, const uint64_t* __restrict__ oval, uint64_t m,
+template <class V>
+__global__ void csr_fill_kernel(const uint64_t* __restrict__ okey, const V* __restrict__ oval, uint64_t m,
                                 int b, const uint64_t* __restrict__ off, const uint8_t* __restrict__ vl,
                                 uint32_t* __restrict__ col, uint32_t* __restrict__ ts, uint8_t* __restrict__ el,
                                 InEdge* __restrict__ rec, uint32_t* __restrict__ ckey) {
     const uint64_t mask = (1ull << b) - 1;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m;
          i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t k = okey[i], v = oval[i];
+        const uint64_t w = okey[i];
+        const uint64_t k = prim::rec_key<V>(w, 2 * b), v = prim::rec_payload<V>(w, oval[i], 2 * b);
         const uint32_t s = (uint32_t)(k >> b), d = (uint32_t)(k & mask);
         const uint32_t t = (uint32_t)(v >> 8), l = (uint32_t)(v & 0xffu);
         col[i] = d;
@@ -279,12 +288,12 @@ __global__ void stats_kernel(const uint64_t* __restrict__ off, const uint64_t* _
 // keys sorted ascending (first, cnt: scratch of n + 1 words; scr: scan scratch
 // of prim::scan_scratch_bytes(n + 1)).
 template <class K>
-int out_offsets(const K* key, uint64_t m, int shift, uint64_t n, uint32_t* first, uint32_t* cnt, uint64_t* off,
-                void* scr, cudaStream_t s) {
+int out_offsets(const K* key, uint64_t m, uint64_t kmask, int shift, uint64_t n, uint32_t* first, uint32_t* cnt,
+                uint64_t* off, void* scr, cudaStream_t s) {
     TP_CUDA(cudaMemsetAsync(first, 0, (n + 1) * 4, s));
     TP_CUDA(cudaMemsetAsync(cnt, 0, (n + 1) * 4, s));
     if (m) {
-        run_ends_kernel<K><<<grid_for(m), kThreads, 0, s>>>(key, m, shift, first, cnt); ::tp::note_launch();
+        run_ends_kernel<K><<<grid_for(m), kThreads, 0, s>>>(key, m, kmask, shift, first, cnt); ::tp::note_launch();
         if (n) { run_count_kernel<<<grid_for(n), kThreads, 0, s>>>(first, cnt, n); ::tp::note_launch(); }
         TP_CUDA(cudaGetLastError());
     }
@@ -338,6 +347,118 @@ struct GraphGuard {  // frees a half-built graph on any error path, after the st
     }
     tripoll_graph* release() { tripoll_graph* r = g; g = nullptr; return r; }
 };
+
+struct DedupIn {
+    const uint32_t *src, *dst, *ts;
+    const uint8_t* el;
+    uint64_t m_in;
+    const uint64_t *eoff, *vbase;
+    uint32_t G;
+    int b;
+    uint64_t sentinel;
+    uint32_t* fault;
+};
+
+// Step 2 with records of value type V: canonical records, their sort by pair, and the minimum
+// payload of every run of equal pairs -- the chronologically first record (Sec. 5.2), label as
+// the tie-break.  ukey/uval receive the unique pairs (sentinel last, if any loops) and payloads
+// as 64-bit words; *m the number of unique pairs without loops.
+template <class V, class Release>
+int dedup(const DedupIn& in, Release release_inputs, Scratch& ukey_d, Scratch& uval_d, uint64_t* m_out,
+          cudaStream_t s) {
+    const uint64_t m_in = in.m_in;
+    const int kb = std::min(64, 2 * in.b);
+    Scratch k0, k1, v0, v1, scr, runs;
+    TP_CUDA(k0.alloc(m_in * 8, s));
+    TP_CUDA(k1.alloc(m_in * 8, s));
+    TP_CUDA(v0.alloc(m_in * sizeof(V), s));
+    TP_CUDA(v1.alloc(m_in * sizeof(V), s));
+    if (m_in)
+        canon_kernel<V><<<grid_for(m_in), kThreads, 0, s>>>(in.src, in.dst, in.ts, in.el, m_in, in.eoff, in.vbase, in.G,
+                                                            in.b, in.sentinel, k0.as<uint64_t>(), v0.as<V>()); ::tp::note_launch();
+    TP_CUDA(cudaGetLastError());
+    release_inputs();
+    const uint64_t tiles = (m_in + prim::kTile - 1) / prim::kTile;
+    TP_CUDA(scr.alloc(std::max(prim::sort_scratch_bytes(m_in), tiles * 12 + prim::scan_scratch_bytes(tiles) + 512), s));
+    bool alt = false;
+    int rc = prim::radix_sort<uint64_t, V>(k0.as<uint64_t>(), k1.as<uint64_t>(), v0.as<V>(), v1.as<V>(), m_in, kb,
+                                           scr.ptr, in.fault, s, &alt);
+    if (rc) return rc;
+    Scratch& kc = alt ? k1 : k0;  // sorted
+    Scratch& vc = alt ? v1 : v0;
+    Scratch& ku = alt ? k0 : k1;  // the unique keys go here
+    (alt ? v0 : v1).release();    // the value buffer not holding the sorted values
+    TP_CUDA(uval_d.alloc(m_in * 8, s));
+    TP_CUDA(runs.alloc(16, s));
+    TP_CUDA(cudaMemsetAsync(runs.ptr, 0, 16, s));
+    if (m_in) {
+        uint32_t* heads = scr.as<uint32_t>();
+        uint64_t* tbase = reinterpret_cast<uint64_t*>(scr.as<unsigned char>() + (tiles * 4 + 255) / 256 * 256);
+        void* sscr = reinterpret_cast<unsigned char*>(tbase) + (tiles * 8 + 255) / 256 * 256;
+        prim::run_heads_kernel<V><<<(unsigned)tiles, prim::kThreads, 0, s>>>(kc.as<uint64_t>(), m_in, kb, heads); ::tp::note_launch();
+        if ((rc = prim::scan<uint64_t, false>(prim::Load<uint32_t, uint64_t>{heads, tiles}, tbase, tiles, sscr, s,
+                                              runs.as<uint64_t>())))
+            return rc;
+        TP_CUDA(cudaMemsetAsync(uval_d.ptr, 0xFF, m_in * 8, s));
+        prim::run_min_kernel<V><<<(unsigned)tiles, prim::kThreads, 0, s>>>(
+            kc.as<uint64_t>(), vc.as<V>(), m_in, kb, tbase, ku.as<uint64_t>(),
+            uval_d.as<unsigned long long>()); ::tp::note_launch();
+        TP_CUDA(cudaGetLastError());
+    }
+    unique_count_kernel<<<1, 1, 0, s>>>(ku.as<uint64_t>(), runs.as<uint64_t>(), in.sentinel, runs.as<uint64_t>() + 1); ::tp::note_launch();
+    TP_CUDA(cudaGetLastError());
+    TP_CUDA(cudaMemcpyAsync(m_out, runs.as<uint64_t>() + 1, 8, cudaMemcpyDeviceToHost, s));
+    TP_CUDA(cudaStreamSynchronize(s));
+    ukey_d.swap(ku);  // keep the unique keys; the other buffers go back when this returns
+    return TRIPOLL_OK;
+}
+
+struct OrientIn {
+    tripoll_graph* g;
+    uint64_t m, n;
+    int b;
+    const uint32_t* rank;
+    uint32_t *first, *cnt;
+    void *sort_scr, *scan_scr;
+    uint32_t* fault;
+    uint32_t* ckey;  // out: target of every edge in CSR order (the key of the in-edge sort)
+};
+
+// Step 5 with records of value type V: every unique pair directed from its <+ -smaller end, sorted
+// by (source, target) position, out-list offsets, the CSR arrays with timestamps and labels
+// aligned (Adj+^m, Sec. 4.2), and the in-edge records in CSR order.  Releases ukey/uval/rank.
+template <class V>
+int orient_csr(const OrientIn& o, Scratch& ukey_d, Scratch& uval_d, Scratch& rank_d, cudaStream_t s) {
+    tripoll_graph* g = o.g;
+    const uint64_t m = o.m;
+    const int kb = std::min(64, 2 * o.b);
+    Scratch ok0, ok1, ov0, ov1;
+    TP_CUDA(ok0.alloc(m * 8, s));
+    TP_CUDA(ok1.alloc(m * 8, s));
+    TP_CUDA(ov0.alloc(m * sizeof(V), s));
+    TP_CUDA(ov1.alloc(m * sizeof(V), s));
+    if (m)
+        orient_kernel<V><<<grid_for(m), kThreads, 0, s>>>(ukey_d.as<uint64_t>(), uval_d.as<uint64_t>(), m, o.b, o.rank,
+                                                          ok0.as<uint64_t>(), ov0.as<V>()); ::tp::note_launch();
+    TP_CUDA(cudaGetLastError());
+    ukey_d.release();
+    uval_d.release();
+    rank_d.release();
+    bool alt = false;
+    int rc = prim::radix_sort<uint64_t, V>(ok0.as<uint64_t>(), ok1.as<uint64_t>(), ov0.as<V>(), ov1.as<V>(), m, kb,
+                                           o.sort_scr, o.fault, s, &alt);
+    if (rc) return rc;
+    const uint64_t* okey = alt ? ok1.as<uint64_t>() : ok0.as<uint64_t>();
+    const V* oval = alt ? ov1.as<V>() : ov0.as<V>();
+    // offsets: out-list lengths from the runs of equal sources (m < 2^32: 32-bit counts are exact)
+    const uint64_t kmask = kb >= 64 ? ~0ull : ((1ull << kb) - 1);
+    if ((rc = out_offsets(okey, m, kmask, o.b, o.n, o.first, o.cnt, g->off, o.scan_scr, s))) return rc;
+    if (m)
+        csr_fill_kernel<V><<<grid_for(m), kThreads, 0, s>>>(okey, oval, m, o.b, g->off, g->vl, g->col, g->ts, g->el,
+                                                            g->in_edge, o.ckey); ::tp::note_launch();
+    TP_CUDA(cudaGetLastError());
+    return TRIPOLL_OK;
+}
 
 int build_impl(const uint32_t* src_h, const uint32_t* dst_h, const uint32_t* ts_h, const uint8_t* el_h,
                uint64_t m_in, const uint8_t* vl_h, uint64_t n, uint32_t Lv, uint32_t Le,
@@ -408,58 +529,19 @@ int build_impl(const uint32_t* src_h, const uint32_t* dst_h, const uint32_t* ts_
     g->has_el = el_h != nullptr;
     g->plan = default_plan();
 
-    // 2. canonical keys + payloads, sort, keep min payload per key run
+    // 2. canonical records, sort, keep the minimum payload of each pair (the chronologically first record)
     uint32_t* fault = flags_d.as<uint32_t>() + 1;  // look-back waits of the radix sorts that gave up
+    const bool packed = 2 * b + 8 <= 64;           // 12-byte records (prim::rec_word)
     uint64_t m = 0;
     Scratch ukey_d, uval_d;
     {
-        Scratch k0, k1, v0, v1, scr, runs;
-        TP_CUDA(k0.alloc(m_in * 8, s));
-        TP_CUDA(k1.alloc(m_in * 8, s));
-        TP_CUDA(v0.alloc(m_in * 8, s));
-        TP_CUDA(v1.alloc(m_in * 8, s));
-        if (m_in)
-            canon_kernel<<<grid_for(m_in), kThreads, 0, s>>>(
-                (const uint32_t*)src.dptr, (const uint32_t*)dst.dptr, (const uint32_t*)ts.dptr,
-                (const uint8_t*)el.dptr, m_in, eoff, vbase, G, b, sentinel, k0.as<uint64_t>(), v0.as<uint64_t>()); ::tp::note_launch();
-        TP_CUDA(cudaGetLastError());
-        src.copy.release(); dst.copy.release(); ts.copy.release(); el.copy.release();
-        const uint64_t tiles = (m_in + prim::kTile - 1) / prim::kTile;
-        TP_CUDA(scr.alloc(std::max(prim::sort_scratch_bytes(m_in), tiles * 12 + prim::scan_scratch_bytes(tiles) + 512), s));
-        bool alt = false;
-        const int end_bit = std::min(64, 2 * b);
-        if ((rc = prim::radix_sort<uint64_t, uint64_t>(k0.as<uint64_t>(), k1.as<uint64_t>(), v0.as<uint64_t>(),
-                                                         v1.as<uint64_t>(), m_in, end_bit, scr.ptr, fault, s, &alt)))
-            return rc;
-        Scratch& kc = alt ? k1 : k0;  // sorted
-        Scratch& vc = alt ? v1 : v0;
-        Scratch& ku = alt ? k0 : k1;  // unique keys and their minimum payloads go here
-        Scratch& vu = alt ? v0 : v1;
-        // the minimum payload of every run of equal keys: the chronologically first record (Sec. 5.2)
-        TP_CUDA(runs.alloc(16, s));
-        TP_CUDA(cudaMemsetAsync(runs.ptr, 0, 16, s));
-        if (m_in) {
-            uint32_t* heads = scr.as<uint32_t>();
-            uint64_t* tbase = reinterpret_cast<uint64_t*>(scr.as<unsigned char>() + (tiles * 4 + 255) / 256 * 256);
-            void* sscr = reinterpret_cast<unsigned char*>(tbase) + (tiles * 8 + 255) / 256 * 256;
-            prim::run_heads_kernel<<<(unsigned)tiles, prim::kThreads, 0, s>>>(kc.as<uint64_t>(), m_in, heads); ::tp::note_launch();
-            if ((rc = prim::scan<uint64_t, false>(prim::Load<uint32_t, uint64_t>{heads, tiles}, tbase, tiles, sscr, s,
-                                                  runs.as<uint64_t>())))
-                return rc;
-            TP_CUDA(cudaMemsetAsync(vu.ptr, 0xFF, m_in * 8, s));
-            prim::run_min_kernel<<<(unsigned)tiles, prim::kThreads, 0, s>>>(
-                kc.as<uint64_t>(), vc.as<uint64_t>(), m_in, tbase, ku.as<uint64_t>(),
-                vu.as<unsigned long long>()); ::tp::note_launch();
-            TP_CUDA(cudaGetLastError());
-        }
-        unique_count_kernel<<<1, 1, 0, s>>>(ku.as<uint64_t>(), runs.as<uint64_t>(), sentinel, runs.as<uint64_t>() + 1); ::tp::note_launch();
-        TP_CUDA(cudaGetLastError());
-        TP_CUDA(cudaMemcpyAsync(&m, runs.as<uint64_t>() + 1, 8, cudaMemcpyDeviceToHost, s));
-        TP_CUDA(cudaStreamSynchronize(s));
+        const DedupIn in{(const uint32_t*)src.dptr, (const uint32_t*)dst.dptr, (const uint32_t*)ts.dptr,
+                         (const uint8_t*)el.dptr, m_in, eoff, vbase, G, b, sentinel, fault};
+        auto release_inputs = [&] { src.copy.release(); dst.copy.release(); ts.copy.release(); el.copy.release(); };
+        rc = packed ? dedup<uint32_t>(in, release_inputs, ukey_d, uval_d, &m, s)
+                    : dedup<uint64_t>(in, release_inputs, ukey_d, uval_d, &m, s);
+        if (rc) return rc;
         if (m >= 0xFFFFFFFFull) return fail(TRIPOLL_ERR_INVALID_ARG, "more than 2^32-2 unique edges");
-        // keep the buffers holding the unique arrays, drop the other two
-        ukey_d.swap(ku);
-        uval_d.swap(vu);
     }
     g->m = m;
 
@@ -527,41 +609,21 @@ int build_impl(const uint32_t* src_h, const uint32_t* dst_h, const uint32_t* ts_
     TP_CUDA(galloc(g, &g->in_off, n + 1, s));
     TP_CUDA(galloc(g, &g->in_edge, m, s));
     {
-        Scratch ok0, ok1, ov1, first, cnt, tmp, sscr;
-        TP_CUDA(ok0.alloc(m * 8, s));
-        TP_CUDA(ok1.alloc(m * 8, s));
-        TP_CUDA(ov1.alloc(m * 8, s));
+        Scratch first, cnt, tmp, sscr, ck0;
         TP_CUDA(first.alloc((n + 1) * 4, s));
         TP_CUDA(cnt.alloc((n + 1) * 4, s));
-        if (m)
-            orient_kernel<<<grid_for(m), kThreads, 0, s>>>(ukey_d.as<uint64_t>(), m, b, rank_d.as<uint32_t>(),
-                                                           ok0.as<uint64_t>()); ::tp::note_launch();
-        TP_CUDA(cudaGetLastError());
-        ukey_d.release();
-        rank_d.release();
-        const int end_bit = std::min(64, 2 * b);
         TP_CUDA(tmp.alloc(prim::sort_scratch_bytes(m), s));
         TP_CUDA(sscr.alloc(prim::scan_scratch_bytes(n + 1), s));
-        bool alt = false;
-        if ((rc = prim::radix_sort<uint64_t, uint64_t>(ok0.as<uint64_t>(), ok1.as<uint64_t>(), uval_d.as<uint64_t>(),
-                                                         ov1.as<uint64_t>(), m, end_bit, tmp.ptr, fault, s, &alt)))
-            return rc;
-        const uint64_t* okey = alt ? ok1.as<uint64_t>() : ok0.as<uint64_t>();
-        const uint64_t* oval = alt ? ov1.as<uint64_t>() : uval_d.as<uint64_t>();
-        // offsets: out-list lengths from the runs of equal sources, exclusive scan
-        // (m < 2^32, so 32-bit counts are exact)
-        if ((rc = out_offsets(okey, m, b, n, first.as<uint32_t>(), cnt.as<uint32_t>(), g->off, sscr.ptr, s))) return rc;
-        // CSR arrays and in-edge records in CSR order; a stable sort by target then
-        // leaves the records in (target, source) order
-        Scratch ck0, ck1, rec1;
         TP_CUDA(ck0.alloc(m * 4, s));
+        // orientation, sort by (source, target), offsets, CSR arrays and the in-edge records in CSR order
+        const OrientIn oin{g, m, n, b, rank_d.as<uint32_t>(), first.as<uint32_t>(), cnt.as<uint32_t>(), tmp.ptr,
+                           sscr.ptr, fault, ck0.as<uint32_t>()};
+        rc = packed ? orient_csr<uint32_t>(oin, ukey_d, uval_d, rank_d, s) : orient_csr<uint64_t>(oin, ukey_d, uval_d, rank_d, s);
+        if (rc) return rc;
+        // a stable sort of the in-edge records by target leaves them in (target, source) order
+        Scratch ck1, rec1;
         TP_CUDA(ck1.alloc(m * 4, s));
         TP_CUDA(rec1.alloc(m * sizeof(InEdge), s));
-        if (m)
-            csr_fill_kernel<<<grid_for(m), kThreads, 0, s>>>(okey, oval, m, b, g->off, g->vl, g->col,
-                                                             g->ts, g->el, g->in_edge, ck0.as<uint32_t>()); ::tp::note_launch();
-        TP_CUDA(cudaGetLastError());
-        ok0.release(); ok1.release(); ov1.release(); uval_d.release();
         const int tbits = std::min(32, b);
         bool ealt = false;
         if ((rc = prim::radix_sort<uint32_t, InEdge>(ck0.as<uint32_t>(), ck1.as<uint32_t>(), g->in_edge,
@@ -574,8 +636,15 @@ int build_impl(const uint32_t* src_h, const uint32_t* dst_h, const uint32_t* ts_
         }
         // in-edge offsets from the runs of equal targets
         const uint32_t* ckey = ealt ? ck1.as<uint32_t>() : ck0.as<uint32_t>();
-        if ((rc = out_offsets(ckey, m, 0, n, first.as<uint32_t>(), cnt.as<uint32_t>(), g->in_off, sscr.ptr, s)))
+        if ((rc = out_offsets(ckey, m, ~0ull, 0, n, first.as<uint32_t>(), cnt.as<uint32_t>(), g->in_off, sscr.ptr, s)))
             return rc;
+        // both lists must account for every edge before anything indexes with these offsets
+        uint64_t ends[2] = {0, 0};
+        TP_CUDA(cudaMemcpyAsync(&ends[0], g->off + n, 8, cudaMemcpyDeviceToHost, s));
+        TP_CUDA(cudaMemcpyAsync(&ends[1], g->in_off + n, 8, cudaMemcpyDeviceToHost, s));
+        TP_CUDA(cudaStreamSynchronize(s));
+        if (ends[0] != m || ends[1] != m)
+            return fail(TRIPOLL_ERR_CUDA, "internal: the out- or in-list offsets of G+ do not add up to its edges");
     }
     (void)vmask;
 

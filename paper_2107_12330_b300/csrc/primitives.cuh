@@ -52,8 +52,11 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     return m;
 }
 
-template <class K> __device__ __forceinline__ uint32_t digit_of(K k, int shift) {
-    return (uint32_t)(k >> shift) & 0xFFu;
+// Digit of key k at bit `shift`, keeping only the bits below end_bit: bits above the sort key may
+// carry other data (a record's payload), which must not take part in the order.
+template <class K> __device__ __forceinline__ uint32_t digit_of(K k, int shift, int end_bit) {
+    const int w = end_bit - shift;
+    return (uint32_t)(k >> shift) & (w >= 8 ? 0xFFu : ((1u << w) - 1u));
 }
 
 // Exclusive prefix of one value per thread over the block (kThreads threads); *total gets the sum.
@@ -84,13 +87,13 @@ __device__ __forceinline__ T block_exclusive_scan(T v, T* s_warp /*[kWarps]*/, T
 
 template <class K>
 __global__ void __launch_bounds__(kThreads) digit_count_kernel(const K* __restrict__ keys, uint64_t n, int passes,
-                                                               uint32_t* __restrict__ counts /*[passes][256]*/) {
+                                                               int end_bit, uint32_t* __restrict__ counts /*[passes][256]*/) {
     __shared__ uint32_t h[8 * kRadix];
     for (int i = threadIdx.x; i < passes * kRadix; i += kThreads) h[i] = 0;
     __syncthreads();
     for (uint64_t i = blockIdx.x * (uint64_t)kThreads + threadIdx.x; i < n; i += (uint64_t)gridDim.x * kThreads) {
         const K k = keys[i];
-        for (int p = 0; p < passes; ++p) atomicAdd(&h[p * kRadix + digit_of(k, 8 * p)], 1u);
+        for (int p = 0; p < passes; ++p) atomicAdd(&h[p * kRadix + digit_of(k, 8 * p, end_bit)], 1u);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < passes * kRadix; i += kThreads)
@@ -120,9 +123,15 @@ __device__ __forceinline__ void cp_async_commit_and_wait_all() {
 
 // Tile shape per key/value type: 8-byte values are staged in digit order for coalesced writes;
 // 16-byte values go out straight from the prefetch buffer (staging them too would cost a block per SM).
+#ifndef TP_SORT_KV_ITEMS
+#define TP_SORT_KV_ITEMS 12  // keys per thread in a sweep that moves values
+#endif
+#ifndef TP_SORT_MIN_BLOCKS
+#define TP_SORT_MIN_BLOCKS 3  // resident blocks per SM the sweep's register budget allows
+#endif
 template <class K, class V> struct SweepShape {
     static constexpr bool kHasValues = !std::is_same<V, NoValue>::value;
-    static constexpr int kItems = kHasValues ? 12 : 16;
+    static constexpr int kItems = kHasValues ? TP_SORT_KV_ITEMS : 16;
     static constexpr int kTile = kThreads * kItems;
     static constexpr bool kStageValues = kHasValues && sizeof(V) <= 8;
     static constexpr size_t kRawBytes = kHasValues ? (size_t)kTile * sizeof(V) : 0;
@@ -131,9 +140,9 @@ template <class K, class V> struct SweepShape {
 };
 
 template <class K, class V>
-__global__ void __launch_bounds__(kThreads, 3) sweep_kernel(const K* __restrict__ kin, K* __restrict__ kout,
+__global__ void __launch_bounds__(kThreads, TP_SORT_MIN_BLOCKS) sweep_kernel(const K* __restrict__ kin, K* __restrict__ kout,
                                                             const V* __restrict__ vin, V* __restrict__ vout, uint64_t n,
-                                                            int shift, const uint32_t* __restrict__ start,
+                                                            int shift, int end_bit, const uint32_t* __restrict__ start,
                                                             unsigned long long* __restrict__ status,
                                                             uint32_t* __restrict__ ticket, uint32_t* __restrict__ fault) {
     using Shape = SweepShape<K, V>;
@@ -175,7 +184,7 @@ __global__ void __launch_bounds__(kThreads, 3) sweep_kernel(const K* __restrict_
 #pragma unroll
     for (int r = 0; r < kIt; ++r) {
         const bool ok = wofs + 32 * r + lane < nv;
-        const uint32_t d = ok ? digit_of(key[r], shift) : (uint32_t)kRadix;  // past the end: a digit of its own
+        const uint32_t d = ok ? digit_of(key[r], shift, end_bit) : (uint32_t)kRadix;  // past the end: a digit of its own
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
         const int leader = __ffs(peers) - 1;
         uint32_t old = 0;
@@ -237,7 +246,7 @@ __global__ void __launch_bounds__(kThreads, 3) sweep_kernel(const K* __restrict_
     for (int r = 0; r < kIt; ++r) {
         lpos[r] = 0xFFFFFFFFu;
         if (wofs + 32 * r + lane < nv) {
-            const uint32_t d = digit_of(key[r], shift);
+            const uint32_t d = digit_of(key[r], shift, end_bit);
             lpos[r] = s_dstart[d] + s_whist[warp][d] + rank[r];
             sk[lpos[r]] = key[r];
         }
@@ -248,7 +257,7 @@ __global__ void __launch_bounds__(kThreads, 3) sweep_kernel(const K* __restrict_
         const uint32_t j = threadIdx.x + r * kThreads;
         if (j < nv) {
             const K k = sk[j];
-            const uint32_t d = digit_of(k, shift);
+            const uint32_t d = digit_of(k, shift, end_bit);
             if constexpr (Shape::kStageValues) s_sdig[j] = (uint8_t)d;
             kout[s_gbase[d] + j] = k;
         }
@@ -272,17 +281,19 @@ __global__ void __launch_bounds__(kThreads, 3) sweep_kernel(const K* __restrict_
 #pragma unroll
             for (int r = 0; r < kIt; ++r)
                 if (lpos[r] != 0xFFFFFFFFu)
-                    vout[s_gbase[digit_of(key[r], shift)] + lpos[r]] = raw[wofs + 32 * r + lane];
+                    vout[s_gbase[digit_of(key[r], shift, end_bit)] + lpos[r]] = raw[wofs + 32 * r + lane];
         }
     }
 }
 
-// Sort n keys (with values when vals != nullptr) by bits [0, end_bit).  keys/vals hold the input;
+// Sort n keys (with values when vals != nullptr) by bits [0, end_bit) (bits above end_bit are carried
+// along and ignored).  keys/vals hold the input;
 // keys_alt/vals_alt are buffers of the same size (16-byte aligned).  On return *in_alt tells where
 // the sorted data is (false: keys/vals, true: keys_alt/vals_alt).  scratch: device memory of
 // sort_scratch_bytes(n).
 inline size_t sort_scratch_bytes(uint64_t n) {
-    const uint64_t tiles = (n + kThreads * 12 - 1) / (kThreads * 12);  // the smallest tile of any shape
+    constexpr uint64_t kMinTile = kThreads * (TP_SORT_KV_ITEMS < 16 ? TP_SORT_KV_ITEMS : 16);  // smallest tile
+    const uint64_t tiles = (n + kMinTile - 1) / kMinTile;
     return 256 + 2 * 8 * kRadix * 4 + tiles * kRadix * 8 + 256;
 }
 
@@ -305,7 +316,7 @@ int radix_sort(K* keys, K* keys_alt, V* vals, V* vals_alt, uint64_t n, int end_b
     TP_CUDA(cudaMemsetAsync(p, 0, 256 + 2 * 8 * kRadix * 4, s));
     {
         const unsigned grid = (unsigned)std::min<uint64_t>((n + kThreads * 8 - 1) / (kThreads * 8), 148u * 8u);
-        digit_count_kernel<K><<<grid, kThreads, 0, s>>>(keys, n, passes, counts); note_launch();
+        digit_count_kernel<K><<<grid, kThreads, 0, s>>>(keys, n, passes, end_bit, counts); note_launch();
         digit_start_kernel<<<passes, kRadix, 0, s>>>(counts, starts); note_launch();
         TP_CUDA(cudaGetLastError());
     }
@@ -325,7 +336,7 @@ int radix_sort(K* keys, K* keys_alt, V* vals, V* vals_alt, uint64_t n, int end_b
         if (trivial) continue;
         TP_CUDA(cudaMemsetAsync(status, 0, tiles * kRadix * 8, s));
         sweep_kernel<K, V><<<(unsigned)tiles, kThreads, Shape::kSmem, s>>>(
-            kcur, knext, vcur, vnext, n, 8 * pass, starts + pass * kRadix, status, ticket + pass, fault);
+            kcur, knext, vcur, vnext, n, 8 * pass, end_bit, starts + pass * kRadix, status, ticket + pass, fault);
         note_launch();
         TP_CUDA(cudaGetLastError());
         std::swap(kcur, knext);
@@ -340,21 +351,38 @@ int radix_sort(K* keys, K* keys_alt, V* vals, V* vals_alt, uint64_t n, int end_b
     return TRIPOLL_OK;
 }
 
-// ---- minimum value per run of equal keys ------------------------------------------------------
+// ---- records: a key with a payload ------------------------------------------------------------
 //
-// keys sorted ascending (equal keys adjacent).  ukey[r], uval[r] = the key of the r-th run and the
-// minimum of its values; the number of runs comes from a scan of the tiles' head counts.  Warp w
-// of a block walks the keys [tile + 32 kItems w, +32 kItems) 32 at a time (lane = position), so
+// The builder sorts records made of a key of kb bits and a 40-bit payload.  The key sits in the low
+// kb bits of a 64-bit word; with a 32-bit value (keys of at most 56 bits) the payload's low 32 bits
+// are the value and its top 8 bits sit above the key in the word, so that a record moves 12 bytes
+// per sort pass; with a 64-bit value the value is the whole payload.  Sorts look only at bits
+// [0, kb) of the word.
+
+template <class V> __host__ __device__ __forceinline__ uint64_t rec_key(uint64_t w, int kb) {
+    return kb >= 64 ? w : (w & ((1ull << kb) - 1));
+}
+template <class V> __host__ __device__ __forceinline__ uint64_t rec_payload(uint64_t w, V v, int kb) {
+    if (sizeof(V) == 4) return ((w >> kb) << 32) | (uint64_t)v;  // kb <= 56 here
+    return (uint64_t)v;
+}
+template <class V> __host__ __device__ __forceinline__ uint64_t rec_word(uint64_t key, uint64_t payload, int kb) {
+    if (sizeof(V) == 4) return key | ((payload >> 32) << kb);
+    return key;
+}
+
+// ---- minimum payload per run of equal keys ----------------------------------------------------
+//
+// Records sorted by key (equal keys adjacent).  ukey[r], uval[r] = the key of the r-th run and the
+// minimum of its payloads; the number of runs comes from a scan of the tiles' head counts.  Warp w
+// of a block walks the records [tile + 32 kItems w, +32 kItems) 32 at a time (lane = position), so
 // loads and the writes of consecutive runs are coalesced.  In each round the lanes of one run are
 // contiguous: a segmented minimum over shuffles leaves the round's part of every run in its last
 // lane, which stores it when the run lies wholly in the round and otherwise combines it with
 // atomicMin (uval must hold ~0 there beforehand: the caller fills uval with 0xFF bytes).
 
-__device__ __forceinline__ bool run_head(const uint64_t* __restrict__ keys, uint64_t i, uint64_t k) {
-    return i == 0 || keys[i - 1] != k;
-}
-
-__global__ void __launch_bounds__(kThreads) run_heads_kernel(const uint64_t* __restrict__ keys, uint64_t n,
+template <class V>
+__global__ void __launch_bounds__(kThreads) run_heads_kernel(const uint64_t* __restrict__ words, uint64_t n, int kb,
                                                              uint32_t* __restrict__ tile_heads) {
     __shared__ uint32_t s_warp[kWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -363,15 +391,16 @@ __global__ void __launch_bounds__(kThreads) run_heads_kernel(const uint64_t* __r
 #pragma unroll 4
     for (int r = 0; r < kItems; ++r) {
         const uint64_t i = lo + 32 * r + lane;
-        if (i < n && run_head(keys, i, keys[i])) ++h;
+        if (i < n && (i == 0 || rec_key<V>(words[i - 1], kb) != rec_key<V>(words[i], kb))) ++h;
     }
     uint32_t total;
     block_exclusive_scan(h, s_warp, &total);
     if (threadIdx.x == 0) tile_heads[blockIdx.x] = total;
 }
 
-__global__ void __launch_bounds__(kThreads) run_min_kernel(const uint64_t* __restrict__ keys,
-                                                           const uint64_t* __restrict__ vals, uint64_t n,
+template <class V>
+__global__ void __launch_bounds__(kThreads) run_min_kernel(const uint64_t* __restrict__ words,
+                                                           const V* __restrict__ vals, uint64_t n, int kb,
                                                            const uint64_t* __restrict__ tile_base,
                                                            uint64_t* __restrict__ ukey,
                                                            unsigned long long* __restrict__ uval) {
@@ -385,8 +414,8 @@ __global__ void __launch_bounds__(kThreads) run_min_kernel(const uint64_t* __res
 #pragma unroll
     for (int r = 0; r < kItems; ++r) {
         const uint64_t i = lo + 32 * r + lane;
-        key[r] = i < n ? keys[i] : 0;
-        const bool h = i < n && run_head(keys, i, key[r]);
+        key[r] = i < n ? rec_key<V>(words[i], kb) : 0;
+        const bool h = i < n && (i == 0 || rec_key<V>(words[i - 1], kb) != key[r]);
         heads |= (h ? 1u : 0u) << r;
         wh += __popc(__ballot_sync(0xffffffffu, h));
     }
@@ -403,7 +432,7 @@ __global__ void __launch_bounds__(kThreads) run_min_kernel(const uint64_t* __res
         // run index: heads at positions <= i, minus one
         const uint64_t run = ok ? run_base + __popc(b & le) - 1 : ~0ull;
         run_base += __popc(b);
-        unsigned long long mn = ok ? (unsigned long long)vals[i] : ~0ull;
+        unsigned long long mn = ok ? (unsigned long long)rec_payload<V>(words[i], vals[i], kb) : ~0ull;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const unsigned long long m2 = __shfl_up_sync(0xffffffffu, mn, o);
@@ -415,8 +444,8 @@ __global__ void __launch_bounds__(kThreads) run_min_kernel(const uint64_t* __res
         if (h) ukey[run] = key[r];
         const bool last_lane = lane == 31 || next_run != run;
         if (!last_lane) continue;
-        // the run ends here when the next position starts another run (or the keys end)
-        const bool ends = lane != 31 || i + 1 == n || keys[i + 1] != key[r];
+        // the run ends here when the next position starts another run (or the records end)
+        const bool ends = lane != 31 || i + 1 == n || rec_key<V>(words[i + 1], kb) != key[r];
         const bool starts = (b & le) != 0;  // its head lies in this round
         if (starts && ends) uval[run] = mn;
         else atomicMin(&uval[run], mn);

@@ -340,3 +340,32 @@ def test_graph_stats():
     assert st["wedges"] == r["stats"]["wedges"]
     assert st["dplus_max"] == r["stats"]["dplus_max"]
     assert st["degree_max"] == r["stats"]["dmax"]
+
+
+def test_vertex_ids_past_2_to_the_28_take_the_wide_record_path():
+    """With n = 2^29 the builder's pair keys take 58 bits, too wide to carry the payload's top byte beside
+    them, so its sorts move the payload as a full 64-bit value instead of the packed 12-byte record.  A
+    sparse graph on 3,000 ids spread over [0, 2^29) must survey exactly like the same graph relabelled onto
+    0..2999 (every table here is invariant under relabelling, Sec. 3), which the oracle surveys."""
+    small = synth.tiny_random_graph(71, 3000, 60000, ts_bits=16, num_vlabels=1, num_elabels=6)
+    n_big = 1 << 29
+    ids = np.unique(synth.uniform_bits(72, synth.STREAM_TS, 4000, 29).astype(np.uint64))[:3000]
+    assert len(ids) == 3000
+    ids = ids[np.argsort(synth.uniform_bits(73, synth.STREAM_TS, 3000, 31), kind="stable")].astype(np.uint32)
+    big = dataclasses.replace(small, name="sparse-2^29", n=n_big, src=ids[small.src], dst=ids[small.dst],
+                              vlabel=None)
+    small = dataclasses.replace(small, vlabel=None)
+    kinds = (tp.TRIPOLL_COUNT | tp.TRIPOLL_CLOSURE_HIST | tp.TRIPOLL_ELABEL_TRIPLES | tp.TRIPOLL_OPEN_CLOSE_HIST |
+             tp.TRIPOLL_DEGREE_TRIPLES)
+    h = tp.tripoll_graph_create(big.src, big.dst, big.ts, big.elabel, None, n_big, 1, 6)
+    try:
+        st = tp.tripoll_graph_stats(h)
+        for window in [(0, 0xFFFFFFFF), (1 << 13, 3 << 13)]:
+            got = np.zeros(tp.tripoll_result_words(kinds, 1, 6, n_big), np.uint64)
+            tp.tripoll_survey(h, kinds, window[0], window[1], got)
+            want, r = oracle_vector(small, kinds, window=window)
+            assert_equal_tables(got, want, kinds, small)
+        # (|W+| is not compared: equal degrees are ordered by id, and relabelling changes that orientation)
+        assert st["num_edges"] == r["stats"]["m"]
+    finally:
+        tp.tripoll_destroy(h)
