@@ -99,25 +99,34 @@ class ClockSampler:
 
 
 # DRAM traffic of the survey per algorithmic byte, from the last ncu capture of
-# survey_block_kernel on R-MAT scale 22 (12.59 GB read, 3.6 MB written, for 9.92 GB
+# survey_block_kernel on R-MAT scale 22 (12.59 GB read, 4.2 MB written, for 9.92 GB
 # of algorithmic bytes), valid only for the survey source it was taken on (first 16
-# hex digits of its SHA-256); any other source reports null.
-PROFILED_SURVEY = {"sha256_16": "143bde6d9ad0d226", "dram_per_alg_byte": (12.586617e9 + 3.648512e6) / 9.917552541e9,
+# hex digits of the SHA-256 of the kernels and their dispatch); any other source
+# reports null.
+PROFILED_SURVEY = {"sha256_16": "c37846c3d53aae99", "dram_per_alg_byte": (12.594253e9 + 4.187904e6) / 9.917552541e9,
                    "capture": "ncu, survey_block_kernel, R-MAT scale 22, scaled by algorithmic bytes"}
 
 
 # The batched family's survey is one survey_warp_kernel launch; DRAM bytes of the
 # timed launch over 2000 graphs of the same family (ncu), per algorithmic byte.
-PROFILED_BATCHED_SURVEY = {"sha256_16": "143bde6d9ad0d226", "dram_per_alg_byte": (1130640128 + 395264) / 3459588372,
+PROFILED_BATCHED_SURVEY = {"sha256_16": "c37846c3d53aae99", "dram_per_alg_byte": (1129550080 + 315392) / 3459588372,
                            "capture": "ncu, survey_warp_kernel, the same family at 2000 graphs, scaled by "
                                       "algorithmic bytes"}
 
 
-def survey_traffic(alg_bytes: int, profiled=None):
+def survey_source_sha16() -> str:
+    """First 16 hex digits of the SHA-256 of the survey kernels' source (kernels, then dispatch)."""
     import hashlib
+    h = hashlib.sha256()
+    for name in ("survey_kernels.cuh", "survey.cu"):
+        with open(os.path.join(ROOT, "paper_2107_12330_b300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def survey_traffic(alg_bytes: int, profiled=None):
     profiled = profiled or PROFILED_SURVEY
-    with open(os.path.join(ROOT, "paper_2107_12330_b300", "csrc", "survey.cu"), "rb") as f:
-        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    sha = survey_source_sha16()
     if sha != profiled["sha256_16"]:
         return None, "survey source changed since the last ncu capture"
     return alg_bytes * profiled["dram_per_alg_byte"], profiled["capture"]

@@ -129,11 +129,17 @@ __device__ __forceinline__ void cp_async_commit_and_wait_all() {
 #ifndef TP_SORT_MIN_BLOCKS
 #define TP_SORT_MIN_BLOCKS 3  // resident blocks per SM the sweep's register budget allows
 #endif
+#ifndef TP_SORT_STAGE16
+#define TP_SORT_STAGE16 0  // stage 16-byte values in digit order too
+#endif
+#ifndef TP_SORT_ITEMS16
+#define TP_SORT_ITEMS16 TP_SORT_KV_ITEMS  // keys per thread in a sweep that moves 16-byte values
+#endif
 template <class K, class V> struct SweepShape {
     static constexpr bool kHasValues = !std::is_same<V, NoValue>::value;
-    static constexpr int kItems = kHasValues ? TP_SORT_KV_ITEMS : 16;
+    static constexpr int kItems = !kHasValues ? 16 : (sizeof(V) > 8 ? TP_SORT_ITEMS16 : TP_SORT_KV_ITEMS);
     static constexpr int kTile = kThreads * kItems;
-    static constexpr bool kStageValues = kHasValues && sizeof(V) <= 8;
+    static constexpr bool kStageValues = kHasValues && (sizeof(V) <= 8 || TP_SORT_STAGE16);
     static constexpr size_t kRawBytes = kHasValues ? (size_t)kTile * sizeof(V) : 0;
     static constexpr size_t kStageBytes = (size_t)kTile * (kStageValues && sizeof(V) > sizeof(K) ? sizeof(V) : sizeof(K));
     static constexpr size_t kSmem = kRawBytes + kStageBytes;
@@ -292,7 +298,8 @@ __global__ void __launch_bounds__(kThreads, TP_SORT_MIN_BLOCKS) sweep_kernel(con
 // the sorted data is (false: keys/vals, true: keys_alt/vals_alt).  scratch: device memory of
 // sort_scratch_bytes(n).
 inline size_t sort_scratch_bytes(uint64_t n) {
-    constexpr uint64_t kMinTile = kThreads * (TP_SORT_KV_ITEMS < 16 ? TP_SORT_KV_ITEMS : 16);  // smallest tile
+    constexpr int kMinItems = TP_SORT_KV_ITEMS < TP_SORT_ITEMS16 ? TP_SORT_KV_ITEMS : TP_SORT_ITEMS16;
+    constexpr uint64_t kMinTile = kThreads * (kMinItems < 16 ? kMinItems : 16);  // the smallest tile of any shape
     const uint64_t tiles = (n + kMinTile - 1) / kMinTile;
     return 256 + 2 * 8 * kRadix * 4 + tiles * kRadix * 8 + 256;
 }

@@ -58,13 +58,16 @@ constexpr uint32_t kSharedTableWords = 4096;  // on-chip mirror of the record pr
 // The mirror holds 32-bit partial sums: 32-bit shared-memory atomics cost less than 64-bit ones.
 // It is moved into the 64-bit record (each word exchanged with 0) often enough that no word
 // can reach 2^32.  A word gains at most one per hit, and an item has at most (staged entries)
-// x (in-edges) hits: 2^11 x 2^11 for block items, 2^7 x 2^6 for warp items.  So a block of a
-// block kernel moves it after every 2^9 items it takes (< 2^31 between moves), and each of the
-// 8 warps of a warp-kernel block after every 2^14 items it takes (< 8 x 2^27 = 2^30).  The
+// x (in-edges) hits: 2^11 x 2^11 for block items, 2^8 x 2^6 for warp items (a plan's warp items
+// hold out-lists of at most 256 entries).  So a block of a block kernel moves it after every 2^9
+// items it takes (< 2^31 between moves), and each of the 8 warps of a warp-kernel block after every
+// 2^14 items it takes (< 8 x 2^28 = 2^31).  The
 // environment variable TRIPOLL_MIRROR_MOVE_LOG2 = k moves it every 2^k items instead when k is
 // smaller (tests use it to exercise the moves on small graphs).
 constexpr uint32_t kBlockMoveLog2 = 9, kWarpMoveLog2 = 14;
-static_assert(kBlockMoveLog2 + 11 + 11 < 32 && kWarpMoveLog2 + 7 + 6 + 3 < 32, "mirror words stay below 2^32");
+static_assert(kBlockMoveLog2 + 11 + 11 < 32 && kWarpMoveLog2 + 8 + 6 + 3 < 32, "mirror words stay below 2^32");
+static_assert(kWarpPlanMax <= (1u << 8) && kItemInEdges <= (1u << 11) && kBigChunk <= (1u << 11),
+              "the plan bounds that the move periods assume");
 using MirrorWord = uint32_t;
 
 // feature bits of a kernel instantiation
