@@ -229,7 +229,7 @@ template <class V>
 __global__ void csr_fill_kernel(const uint64_t* __restrict__ okey, const V* __restrict__ oval, uint64_t m,
                                 int b, const uint64_t* __restrict__ off, const uint8_t* __restrict__ vl,
                                 uint32_t* __restrict__ col, uint32_t* __restrict__ ts, uint8_t* __restrict__ el,
-                                InEdge* __restrict__ rec, uint32_t* __restrict__ ckey) {
+                                InEdge* __restrict__ rec, uint32_t* __restrict__ ckey, uint32_t* __restrict__ cpos) {
     const uint64_t mask = (1ull << b) - 1;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m;
          i += (uint64_t)gridDim.x * blockDim.x) {
@@ -247,7 +247,16 @@ __global__ void csr_fill_kernel(const uint64_t* __restrict__ okey, const V* __re
         ie.meta = l | ((uint32_t)vl[s] << 8);
         rec[i] = ie;
         ckey[i] = d;
+        cpos[i] = (uint32_t)i;
     }
+}
+
+// The in-edge records in (target, source) order: record k is the CSR-order record at the position
+// the sort of (target, position) pairs left at k.
+__global__ void gather_in_edges_kernel(const InEdge* __restrict__ csr_rec, const uint32_t* __restrict__ pos,
+                                       uint64_t m, InEdge* __restrict__ out) {
+    for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < m; k += (uint64_t)gridDim.x * blockDim.x)
+        out[k] = csr_rec[pos[k]];
 }
 
 __global__ void vlabel_pos_kernel(const uint8_t* __restrict__ vl, const uint32_t* __restrict__ order, uint64_t n,
@@ -422,6 +431,8 @@ struct OrientIn {
     void *sort_scr, *scan_scr;
     uint32_t* fault;
     uint32_t* ckey;  // out: target of every edge in CSR order (the key of the in-edge sort)
+    uint32_t* cpos;  // out: the CSR position of every edge (the value of the in-edge sort)
+    InEdge* rec;     // out: the in-edge records in CSR order
 };
 
 // Step 5 with records of value type V: every unique pair directed from its <+ -smaller end, sorted
@@ -455,7 +466,7 @@ int orient_csr(const OrientIn& o, Scratch& ukey_d, Scratch& uval_d, Scratch& ran
     if ((rc = out_offsets(okey, m, kmask, o.b, o.n, o.first, o.cnt, g->off, o.scan_scr, s))) return rc;
     if (m)
         csr_fill_kernel<V><<<grid_for(m), kThreads, 0, s>>>(okey, oval, m, o.b, g->off, g->vl, g->col, g->ts, g->el,
-                                                            g->in_edge, o.ckey); ::tp::note_launch();
+                                                            o.rec, o.ckey, o.cpos); ::tp::note_launch();
     TP_CUDA(cudaGetLastError());
     return TRIPOLL_OK;
 }
@@ -609,31 +620,34 @@ int build_impl(const uint32_t* src_h, const uint32_t* dst_h, const uint32_t* ts_
     TP_CUDA(galloc(g, &g->in_off, n + 1, s));
     TP_CUDA(galloc(g, &g->in_edge, m, s));
     {
-        Scratch first, cnt, tmp, sscr, ck0;
+        Scratch first, cnt, tmp, sscr, ck0, cp0, rec0;
         TP_CUDA(first.alloc((n + 1) * 4, s));
         TP_CUDA(cnt.alloc((n + 1) * 4, s));
         TP_CUDA(tmp.alloc(prim::sort_scratch_bytes(m), s));
         TP_CUDA(sscr.alloc(prim::scan_scratch_bytes(n + 1), s));
         TP_CUDA(ck0.alloc(m * 4, s));
+        TP_CUDA(cp0.alloc(m * 4, s));
+        TP_CUDA(rec0.alloc(m * sizeof(InEdge), s));
         // orientation, sort by (source, target), offsets, CSR arrays and the in-edge records in CSR order
         const OrientIn oin{g, m, n, b, rank_d.as<uint32_t>(), first.as<uint32_t>(), cnt.as<uint32_t>(), tmp.ptr,
-                           sscr.ptr, fault, ck0.as<uint32_t>()};
+                           sscr.ptr, fault, ck0.as<uint32_t>(), cp0.as<uint32_t>(), rec0.as<InEdge>()};
         rc = packed ? orient_csr<uint32_t>(oin, ukey_d, uval_d, rank_d, s) : orient_csr<uint64_t>(oin, ukey_d, uval_d, rank_d, s);
         if (rc) return rc;
-        // a stable sort of the in-edge records by target leaves them in (target, source) order
-        Scratch ck1, rec1;
+        // a stable sort of (target, CSR position) pairs by target leaves the positions in (target, source)
+        // order; the 16-byte records are then gathered once in that order
+        Scratch ck1, cp1;
         TP_CUDA(ck1.alloc(m * 4, s));
-        TP_CUDA(rec1.alloc(m * sizeof(InEdge), s));
+        TP_CUDA(cp1.alloc(m * 4, s));
         const int tbits = std::min(32, b);
         bool ealt = false;
-        if ((rc = prim::radix_sort<uint32_t, InEdge>(ck0.as<uint32_t>(), ck1.as<uint32_t>(), g->in_edge,
-                                                       rec1.as<InEdge>(), m, tbits, tmp.ptr, fault, s, &ealt)))
+        if ((rc = prim::radix_sort<uint32_t, uint32_t>(ck0.as<uint32_t>(), ck1.as<uint32_t>(), cp0.as<uint32_t>(),
+                                                         cp1.as<uint32_t>(), m, tbits, tmp.ptr, fault, s, &ealt)))
             return rc;
-        if (ealt) {  // the sorted records are in the second buffer: keep that one
-            InEdge* sorted_rec = rec1.as<InEdge>();
-            swap_block(g, g->in_edge, rec1);
-            g->in_edge = sorted_rec;
-        }
+        if (m)
+            gather_in_edges_kernel<<<grid_for(m), kThreads, 0, s>>>(rec0.as<InEdge>(),
+                                                                    (ealt ? cp1 : cp0).as<uint32_t>(), m,
+                                                                    g->in_edge); ::tp::note_launch();
+        TP_CUDA(cudaGetLastError());
         // in-edge offsets from the runs of equal targets
         const uint32_t* ckey = ealt ? ck1.as<uint32_t>() : ck0.as<uint32_t>();
         if ((rc = out_offsets(ckey, m, ~0ull, 0, n, first.as<uint32_t>(), cnt.as<uint32_t>(), g->in_off, sscr.ptr, s)))

@@ -42,6 +42,7 @@ constexpr uint64_t kFlagAggregate = 1ull << 62;  // the tile's own counts are pu
 constexpr uint64_t kFlagInclusive = 2ull << 62;  // counts of all tiles up to this one are published
 constexpr uint64_t kValueMask = (1ull << 62) - 1;
 constexpr uint32_t kSpinLimit = 1u << 22;
+constexpr int kLookback = 8;  // predecessors a look-back round reads at once
 constexpr uint32_t kFaultLookback = 1u;  // a look-back wait gave up
 
 static_assert(kThreads == kRadix, "one thread per digit in the look-back");
@@ -132,6 +133,12 @@ __device__ __forceinline__ void cp_async_commit_and_wait_all() {
 #ifndef TP_SORT_STAGE16
 #define TP_SORT_STAGE16 0  // stage 16-byte values in digit order too
 #endif
+#ifndef TP_SORT_STAGE8
+#define TP_SORT_STAGE8 1  // stage values of up to 8 bytes in digit order
+#endif
+#ifndef TP_SORT_RANK_ATOMIC
+#define TP_SORT_RANK_ATOMIC 1  // the ranking leader bumps its warp counter with one shared atomic
+#endif
 #ifndef TP_SORT_ITEMS16
 #define TP_SORT_ITEMS16 TP_SORT_KV_ITEMS  // keys per thread in a sweep that moves 16-byte values
 #endif
@@ -139,7 +146,7 @@ template <class K, class V> struct SweepShape {
     static constexpr bool kHasValues = !std::is_same<V, NoValue>::value;
     static constexpr int kItems = !kHasValues ? 16 : (sizeof(V) > 8 ? TP_SORT_ITEMS16 : TP_SORT_KV_ITEMS);
     static constexpr int kTile = kThreads * kItems;
-    static constexpr bool kStageValues = kHasValues && (sizeof(V) <= 8 || TP_SORT_STAGE16);
+    static constexpr bool kStageValues = kHasValues && (sizeof(V) <= 8 ? TP_SORT_STAGE8 : TP_SORT_STAGE16);
     static constexpr size_t kRawBytes = kHasValues ? (size_t)kTile * sizeof(V) : 0;
     static constexpr size_t kStageBytes = (size_t)kTile * (kStageValues && sizeof(V) > sizeof(K) ? sizeof(V) : sizeof(K));
     static constexpr size_t kSmem = kRawBytes + kStageBytes;
@@ -149,16 +156,18 @@ template <class K, class V>
 __global__ void __launch_bounds__(kThreads, TP_SORT_MIN_BLOCKS) sweep_kernel(const K* __restrict__ kin, K* __restrict__ kout,
                                                             const V* __restrict__ vin, V* __restrict__ vout, uint64_t n,
                                                             int shift, int end_bit, const uint32_t* __restrict__ start,
-                                                            unsigned long long* __restrict__ status,
+                                                            unsigned long long* __restrict__ status, uint64_t tiles,
                                                             uint32_t* __restrict__ ticket, uint32_t* __restrict__ fault) {
     using Shape = SweepShape<K, V>;
     constexpr int kIt = Shape::kItems;
     constexpr int kT = Shape::kTile;
     extern __shared__ __align__(16) unsigned char smem[];  // [raw values in input order][stage]
     __shared__ uint32_t s_tile;
-    __shared__ uint32_t s_whist[kWarps][kRadix];  // per-warp digit counts, then each warp's offset in the digit
-    __shared__ uint32_t s_dstart[kRadix];         // tile-local start of each digit
-    __shared__ unsigned long long s_gbase[kRadix];  // output position of tile-local index 0 of each digit
+    // per-warp digit counts, then the tile-local position of each warp's first key of each digit
+    __shared__ uint32_t s_whist[kWarps][kRadix];
+    // output position of tile-local index 0 of each digit, modulo 2^32 (positions are below 2^32, so
+    // base + index modulo 2^32 is the position even when the base itself wraps)
+    __shared__ uint32_t s_gbase[kRadix];
     __shared__ uint32_t s_warp_tmp[kWarps];
     __shared__ uint8_t s_sdig[Shape::kStageValues ? kT : 1];  // digit of each staged (sorted) key
 
@@ -195,8 +204,12 @@ __global__ void __launch_bounds__(kThreads, TP_SORT_MIN_BLOCKS) sweep_kernel(con
         const int leader = __ffs(peers) - 1;
         uint32_t old = 0;
         if (lane == leader && ok) {
+#if TP_SORT_RANK_ATOMIC
+            old = atomicAdd(&s_whist[warp][d], (uint32_t)__popc(peers));
+#else
             old = s_whist[warp][d];
             s_whist[warp][d] = old + __popc(peers);
+#endif
         }
         rank[r] = __shfl_sync(0xffffffffu, old, leader) + __popc(peers & lt);
         __syncwarp();  // the next round's leaders (other lanes) read these counters
@@ -205,44 +218,56 @@ __global__ void __launch_bounds__(kThreads, TP_SORT_MIN_BLOCKS) sweep_kernel(con
 
     // per digit (thread = digit): offsets of the warps within the tile's run of that digit
     const uint32_t dg = threadIdx.x;
-    uint32_t cnt = 0;
+    uint32_t cnt = 0, wofs_d[kWarps];
 #pragma unroll
     for (int w = 0; w < kWarps; ++w) {
-        const uint32_t x = s_whist[w][dg];
-        s_whist[w][dg] = cnt;
-        cnt += x;
+        wofs_d[w] = cnt;
+        cnt += s_whist[w][dg];
     }
     uint32_t tile_total;
     const uint32_t dstart = block_exclusive_scan(cnt, s_warp_tmp, &tile_total);
-    s_dstart[dg] = dstart;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) s_whist[w][dg] = dstart + wofs_d[w];  // where warp w's keys of dg start
 
-    // decoupled look-back: keys of digit dg in all earlier tiles
-    volatile unsigned long long* vs = status;
+    // decoupled look-back: keys of digit dg in all earlier tiles.  Status words are [tile][digit]
+    // (a warp reads 32 digits of one tile in one line), and each round reads the next kLookback
+    // predecessors at once: a tile usually finds its nearest predecessor with an inclusive prefix
+    // several tiles back (tiles start a few tens of ns apart, an L2 round trip takes hundreds), so
+    // reading them one at a time would make the walk a chain of round trips.
+    volatile unsigned long long* col = status + dg;  // digit dg of tile t at col[t * kRadix]
     unsigned long long excl = 0;
     if (tile == 0) {
-        vs[dg] = kFlagInclusive | cnt;
+        col[0] = kFlagInclusive | cnt;
     } else {
-        vs[tile * kRadix + dg] = kFlagAggregate | cnt;
-        uint64_t j = tile - 1;
-        uint32_t spins = 0;
-        while (true) {
-            const unsigned long long st = vs[j * kRadix + dg];
-            const unsigned long long flag = st & ~kValueMask;
-            if (flag == 0) {
-                if (++spins > kSpinLimit) {
-                    atomicOr(fault, kFaultLookback);
-                    break;
+        col[tile * kRadix] = kFlagAggregate | cnt;
+        uint64_t j = tile;  // predecessors below j are still to be read
+        bool done = false;
+        while (!done && j > 0) {
+            unsigned long long st[kLookback];
+#pragma unroll
+            for (int i = 0; i < kLookback; ++i) st[i] = (j > (uint64_t)i) ? col[(j - 1 - i) * kRadix] : kFlagInclusive;
+#pragma unroll
+            for (int i = 0; i < kLookback; ++i) {
+                if (done) break;
+                unsigned long long v = st[i];
+                uint32_t spins = 0;
+                while ((v & ~kValueMask) == 0) {  // not published yet: wait for this one
+                    if (++spins > kSpinLimit) {
+                        atomicOr(fault, kFaultLookback);
+                        v = kFlagInclusive;  // give up; the tile's writes stay inside its digits' ranges
+                        break;
+                    }
+                    __nanosleep(spins < 64 ? 32 : 256);
+                    v = col[(j - 1 - i) * kRadix];
                 }
-                __nanosleep(spins < 64 ? 32 : 256);
-                continue;
+                excl += v & kValueMask;
+                if ((v & ~kValueMask) == kFlagInclusive) done = true;
             }
-            excl += st & kValueMask;
-            if (flag == kFlagInclusive || j == 0) break;
-            --j;
+            j = j > (uint64_t)kLookback ? j - kLookback : 0;
         }
-        vs[tile * kRadix + dg] = kFlagInclusive | (excl + cnt);
+        col[tile * kRadix] = kFlagInclusive | (excl + cnt);
     }
-    s_gbase[dg] = (unsigned long long)start[dg] + excl - dstart;
+    s_gbase[dg] = (uint32_t)((unsigned long long)start[dg] + excl - dstart);
     __syncthreads();
 
     // stage the keys in digit order, then write them out in runs of equal digits
@@ -253,7 +278,7 @@ __global__ void __launch_bounds__(kThreads, TP_SORT_MIN_BLOCKS) sweep_kernel(con
         lpos[r] = 0xFFFFFFFFu;
         if (wofs + 32 * r + lane < nv) {
             const uint32_t d = digit_of(key[r], shift, end_bit);
-            lpos[r] = s_dstart[d] + s_whist[warp][d] + rank[r];
+            lpos[r] = s_whist[warp][d] + rank[r];
             sk[lpos[r]] = key[r];
         }
     }
@@ -343,7 +368,7 @@ int radix_sort(K* keys, K* keys_alt, V* vals, V* vals_alt, uint64_t n, int end_b
         if (trivial) continue;
         TP_CUDA(cudaMemsetAsync(status, 0, tiles * kRadix * 8, s));
         sweep_kernel<K, V><<<(unsigned)tiles, kThreads, Shape::kSmem, s>>>(
-            kcur, knext, vcur, vnext, n, 8 * pass, end_bit, starts + pass * kRadix, status, ticket + pass, fault);
+            kcur, knext, vcur, vnext, n, 8 * pass, end_bit, starts + pass * kRadix, status, tiles, ticket + pass, fault);
         note_launch();
         TP_CUDA(cudaGetLastError());
         std::swap(kcur, knext);
