@@ -123,11 +123,12 @@ struct GraphDev {
     const uint32_t* graph_of = nullptr; // [n] graph index by position (batched) or null
     const uint64_t* in_off = nullptr;   // [n+1]
     const InEdge* in_edge = nullptr;    // [m]
-    // Window view: when set, col/ts/el above hold only the edges whose timestamp
-    // lies in the survey's window (same order), and newpos[e] (e in [0, m]) is
-    // the number of such edges before CSR position e of G+; off, in_off and
-    // in_edge stay those of G+ and are translated through newpos.
-    const uint32_t* newpos = nullptr;   // [m+1] or null
+    // Window view: when set, col/ts/el above hold only the edges whose timestamp lies in the survey's
+    // window (same order), and vidx tells where CSR position e of G+ (e in [0, m]) lands in it: word
+    // vidx[e >> 5] holds the in-window edges before position 32 (e >> 5) and the in-window bits of
+    // those 32 positions (view_pos).  off, in_off and in_edge stay those of G+ and are translated
+    // through vidx.  (8 bytes per 32 edges: the index stays in L2 on large graphs.)
+    const uint2* vidx = nullptr;        // [(m >> 5) + 1] or null
     const uint32_t* vorig = nullptr;    // [m] CSR position in G+ of each view entry (per-edge counts only)
 };
 

@@ -158,24 +158,39 @@ unsigned grid_n(uint64_t items) {
 // with a window holding a fraction f of the edges, the checks drop from about
 // f |W+| (in-place skipping of (p,q) and (q,r) only) to about f^2 |W+|.
 
-// 1 for CSR positions e < m whose timestamp lies in the window, 0 for e = m.
-struct InWindow {
-    const uint32_t* ts;
-    uint64_t m;
-    uint32_t lo, hi;
-    __host__ __device__ uint32_t operator()(uint64_t e) const {
-        return (e < m && ts[e] >= lo && ts[e] <= hi) ? 1u : 0u;
+// The window view's index, first part: per 32 CSR positions (a warp), the in-window bits (into
+// vidx[w].y) and their count (the input of the scan that gives vidx[w].x).
+__global__ void view_bits_kernel(const uint32_t* __restrict__ ts, uint64_t m, uint64_t words, uint32_t lo,
+                                 uint32_t hi, uint2* __restrict__ vidx, uint32_t* __restrict__ cnt) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;  // a multiple of 32: warps stay aligned
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < words * 32; e += stride) {
+        bool in = false;
+        if (e < m) {
+            const uint32_t t = ts[e];
+            in = t >= lo && t <= hi;
+        }
+        const unsigned bits = __ballot_sync(0xffffffffu, in);
+        if ((threadIdx.x & 31) == 0) {
+            vidx[e >> 5].y = bits;
+            cnt[e >> 5] = __popc(bits);
+        }
     }
-};
+}
+
+__global__ void view_prefix_kernel(const uint32_t* __restrict__ pre, uint64_t words, uint2* __restrict__ vidx) {
+    for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < words; w += (uint64_t)gridDim.x * blockDim.x)
+        vidx[w].x = pre[w];
+}
 
 __global__ void window_view_kernel(const uint32_t* __restrict__ col, const uint32_t* __restrict__ ts,
-                                   const uint8_t* __restrict__ el, const uint32_t* __restrict__ newpos, uint64_t m,
+                                   const uint8_t* __restrict__ el, const uint2* __restrict__ vidx, uint64_t m,
                                    uint32_t lo, uint32_t hi, uint32_t* __restrict__ vcol, uint32_t* __restrict__ vts,
                                    uint8_t* __restrict__ vel, uint32_t* __restrict__ vorig) {
     for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < m; e += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t t = ts[e];
         if (t < lo || t > hi) continue;
-        const uint32_t p = newpos[e];
+        const uint2 w = vidx[e >> 5];
+        const uint32_t p = w.x + __popc(w.y & ((1u << (e & 31u)) - 1u));
         vcol[p] = col[e];
         vts[p] = t;
         if (el) vel[p] = el[e];
@@ -183,7 +198,8 @@ __global__ void window_view_kernel(const uint32_t* __restrict__ col, const uint3
     }
 }
 
-size_t window_scan_bytes(uint64_t m) { return prim::scan_scratch_bytes(m + 1); }
+uint64_t view_words(uint64_t m) { return (m >> 5) + 1; }
+size_t window_scan_bytes(uint64_t m) { return prim::scan_scratch_bytes(view_words(m)); }
 constexpr LaunchFn kLaunch[64] = {
     &launch_f<0>,  &launch_f<1>,  &launch_f<2>,  &launch_f<3>,  &launch_f<4>,  &launch_f<5>,  &launch_f<6>,
     &launch_f<7>,  &launch_f<8>,  &launch_f<9>,  &launch_f<10>, &launch_f<11>, &launch_f<12>, &launch_f<13>,
@@ -286,7 +302,8 @@ uint64_t window_view_bytes(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo
     if ((t_lo == 0 && t_hi == 0xFFFFFFFFu) || !g->m) return 0;
     const uint64_t m = g->m;
     const uint64_t r = 256;  // pool rounding per allocation
-    return (m + 1) * 4 + r + 2 * ((m + kColPad) * 4 + r) + (g->el ? m + kColPad + r : 0) +
+    const uint64_t w = view_words(m);
+    return (w * 8 + r) + 2 * (w * 4 + r) + 2 * ((m + kColPad) * 4 + r) + (g->el ? m + kColPad + r : 0) +
            ((kinds & TRIPOLL_EDGE_LOCAL) ? m * 4 + r : 0) + window_scan_bytes(m) + r;
 }
 
@@ -365,19 +382,25 @@ int launch_survey(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_
     }
     mark(ev, 0, s);
     GraphDev gd = g->dev();
-    Scratch vpos, vcol, vts, vel, vorig, vtmp;  // released (stream-ordered) after the survey kernels
+    Scratch vx, vcnt, vpre, vcol, vts, vel, vorig, vtmp;  // released (stream-ordered) after the survey kernels
     if (window && window_view && g->m) {
-        const uint64_t m = g->m;
-        TP_CUDA(vpos.alloc((m + 1) * 4, s));
+        const uint64_t m = g->m, words = view_words(m);
+        TP_CUDA(vx.alloc(words * 8, s));
+        TP_CUDA(vcnt.alloc(words * 4, s));
+        TP_CUDA(vpre.alloc(words * 4, s));
         TP_CUDA(vcol.alloc((m + kColPad) * 4, s));
         TP_CUDA(vts.alloc((m + kColPad) * 4, s));
         if (g->el) TP_CUDA(vel.alloc(m + kColPad, s));
         if (kinds & TRIPOLL_EDGE_LOCAL) TP_CUDA(vorig.alloc(m * 4, s));
         TP_CUDA(vtmp.alloc(window_scan_bytes(m), s));
+        view_bits_kernel<<<grid_n(words * 32), 256, 0, s>>>(g->ts, m, words, t_lo, t_hi, vx.as<uint2>(),
+                                                            vcnt.as<uint32_t>()); ::tp::note_launch();
         int rc;
-        if ((rc = prim::scan<uint32_t, false>(InWindow{g->ts, m, t_lo, t_hi}, vpos.as<uint32_t>(), m + 1, vtmp.ptr, s)))
+        if ((rc = prim::scan<uint32_t, false>(prim::Load<uint32_t, uint32_t>{vcnt.as<uint32_t>(), words},
+                                              vpre.as<uint32_t>(), words, vtmp.ptr, s)))
             return rc;
-        window_view_kernel<<<grid_n(m), 256, 0, s>>>(g->col, g->ts, g->el, vpos.as<uint32_t>(), m, t_lo, t_hi,
+        view_prefix_kernel<<<grid_n(words), 256, 0, s>>>(vpre.as<uint32_t>(), words, vx.as<uint2>()); ::tp::note_launch();
+        window_view_kernel<<<grid_n(m), 256, 0, s>>>(g->col, g->ts, g->el, vx.as<uint2>(), m, t_lo, t_hi,
                                                      vcol.as<uint32_t>(), vts.as<uint32_t>(),
                                                      g->el ? vel.as<uint8_t>() : nullptr,
                                                      vorig.as<uint32_t>()); ::tp::note_launch();
@@ -385,7 +408,7 @@ int launch_survey(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_
         gd.col = vcol.as<uint32_t>();
         gd.ts = vts.as<uint32_t>();
         gd.el = g->el ? vel.as<uint8_t>() : nullptr;
-        gd.newpos = vpos.as<uint32_t>();
+        gd.vidx = vx.as<uint2>();
         gd.vorig = vorig.as<uint32_t>();
     }
     kLaunch[F](g, gd, a, s, sms, ev);

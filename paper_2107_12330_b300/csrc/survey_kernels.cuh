@@ -291,6 +291,12 @@ __device__ __forceinline__ void fold_warp(bool keep, const TriMeta& t, const Sur
 
 __device__ __forceinline__ bool in_window(uint32_t t, uint32_t lo, uint32_t hi) { return t >= lo && t <= hi; }
 
+// Position in the window view of CSR position e of G+: in-window edges before e.
+__device__ __forceinline__ uint32_t view_pos(const uint2* __restrict__ vidx, uint32_t e) {
+    const uint2 w = __ldg(&vidx[e >> 5]);
+    return w.x + __popc(w.y & ((1u << (e & 31u)) - 1u));
+}
+
 // First index in [lo, hi) with col[idx] >= v.
 __device__ __forceinline__ uint32_t lower_bound_col(const uint32_t* __restrict__ col, uint32_t lo, uint32_t hi,
                                                     uint32_t v) {
@@ -447,9 +453,9 @@ __device__ __forceinline__ uint32_t stage_in_edge(const GraphDev& g, const Surve
         p = lo;
     }
     uint32_t j0 = ie.e + 1, jend = ie.end;
-    if (ok && g.newpos) {  // the suffix of Adj+(p) after q in the window view
-        j0 = __ldg(&g.newpos[ie.e]) + 1;
-        jend = __ldg(&g.newpos[ie.end]);
+    if (ok && g.vidx) {  // the suffix of Adj+(p) after q in the window view
+        j0 = view_pos(g.vidx, ie.e) + 1;
+        jend = view_pos(g.vidx, ie.end);
     }
     if (ok && chunked && j0 < jend) {
         j0 = lower_bound_col(g.col, j0, jend, vlo);
@@ -803,16 +809,16 @@ __global__ void __launch_bounds__(kBlockThreads, CHUNK <= kBlockChunk ? 5 : 3)
         grec_prev = grec;
         uint32_t qbase = (uint32_t)g.off[q] + item.qlo;
         uint32_t len = item.qlen;
-        if (g.newpos) {  // the item's part of Adj+(q) in the window view
-            const uint32_t b0 = __ldg(&g.newpos[qbase]);
-            len = __ldg(&g.newpos[qbase + len]) - b0;
+        if (g.vidx) {  // the item's part of Adj+(q) in the window view
+            const uint32_t b0 = view_pos(g.vidx, qbase);
+            len = view_pos(g.vidx, qbase + len) - b0;
             qbase = b0;
             if (len == 0) {  // no in-window (q,r): no triangle; s_item is read by all before it changes
                 __syncthreads();
                 continue;
             }
         }
-        T.size = view_table_size(len, g.newpos != nullptr, kBlockTable);
+        T.size = view_table_size(len, g.vidx != nullptr, kBlockTable);
         const uint32_t tsize = T.size;
         for (uint32_t i = threadIdx.x; i < tsize; i += blockDim.x) T.key[i] = kEmpty;
         __syncthreads();
@@ -895,9 +901,9 @@ __global__ void __launch_bounds__(kBlockThreads, 5) survey_warp_kernel(GraphDev 
         grec_prev = grec;
         uint32_t qbase = (uint32_t)g.off[q];
         uint32_t len = item.qlen;
-        if (g.newpos) {  // Adj+(q) in the window view
-            const uint32_t b0 = __ldg(&g.newpos[qbase]);
-            len = __ldg(&g.newpos[qbase + len]) - b0;
+        if (g.vidx) {  // Adj+(q) in the window view
+            const uint32_t b0 = view_pos(g.vidx, qbase);
+            len = view_pos(g.vidx, qbase + len) - b0;
             qbase = b0;
             if (len == 0) continue;  // no in-window (q,r): no triangle
         }
@@ -909,7 +915,7 @@ __global__ void __launch_bounds__(kBlockThreads, 5) survey_warp_kernel(GraphDev 
         // leaves more in it); each part restricts the suffixes to its value range
         for (uint32_t c0 = 0; c0 < len; c0 += kWarpMaxQ) {
             const uint32_t clen = min(kWarpMaxQ, len - c0);
-            T.size = view_table_size(clen, g.newpos != nullptr, kWTable);
+            T.size = view_table_size(clen, g.vidx != nullptr, kWTable);
             const uint32_t tsize = T.size;
             __syncwarp();
             for (uint32_t i = lane; i < tsize; i += 32) ws.key[i] = kEmpty;
