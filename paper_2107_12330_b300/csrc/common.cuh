@@ -98,9 +98,9 @@ struct __align__(16) InEdge {
     uint32_t meta;
 };
 
-// A unit of survey work: middle vertex q, the part [qlo, qlo + qlen) of its
-// out-list staged on chip (CSR positions [qpos, qpos + qlen) of G+), and the
-// in-edges [in_lo, in_hi) of q whose pivot suffixes are checked against it.
+// A unit of survey work: middle vertex q, the part [qlo, qhi) of its out-list
+// staged on chip, and the in-edges [in_lo, in_hi) of q whose pivot suffixes
+// are checked against it.
 struct __align__(16) WorkItem {
     uint32_t q;
     uint32_t qlo;     // offset into q's out-list
@@ -108,8 +108,7 @@ struct __align__(16) WorkItem {
     uint32_t in_lo;   // into in_edge[], absolute
     uint32_t in_hi;
     uint32_t flags;   // bit 0: chunked (restrict suffix to the staged value range)
-    uint32_t qpos;    // off[q] + qlo: the part's first CSR position
-    uint32_t pad;
+    uint32_t pad0, pad1;
 };
 
 struct GraphDev {

@@ -137,8 +137,7 @@ __global__ void plan_fill_kernel(const uint64_t* __restrict__ off, const uint64_
                 it.in_lo = ilo + (uint32_t)s;
                 it.in_hi = ilo + (uint32_t)umin64(di, s + per);
                 it.flags = chunked ? 1u : 0u;
-                it.qpos = (uint32_t)(off[q] + c);
-                it.pad = 0;
+                it.pad0 = it.pad1 = 0;
                 dst[o++] = it;
             }
         }

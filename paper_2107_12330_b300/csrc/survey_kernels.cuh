@@ -434,24 +434,11 @@ __device__ __forceinline__ uint32_t upper_bound_col(const uint32_t* __restrict__
     return lo;
 }
 
-// The suffix [j0, jend) of Adj+(p) after q for in-edge record ie, in the surveyed arrays: the window
-// view's positions when surveying one (two gathers from its index), else those of G+.  An in-edge
-// outside the window checks nothing, so its suffix is not translated.
-template <int F>
-__device__ __forceinline__ uint2 suffix_of(const GraphDev& g, const SurveyArgs& a, const InEdge& ie) {
-    uint2 sfx = make_uint2(ie.e + 1, ie.end);
-    if (g.vidx && (!(F & F_TS) || in_window(ie.ts, a.t_lo, a.t_hi))) {
-        sfx.x = view_pos(g.vidx, ie.e) + 1;
-        sfx.y = view_pos(g.vidx, ie.end);
-    }
-    return sfx;
-}
-
-// Stage in-edge record ie (its suffix sfx from suffix_of) in slot k; returns its segment's unit count.
+// Stage in-edge slot k (absolute record kk); returns its segment's unit count.
 template <int F>
 __device__ __forceinline__ uint32_t stage_in_edge(const GraphDev& g, const SurveyArgs& a, InStage S, uint32_t k,
-                                                  const InEdge& ie, uint2 sfx, bool chunked, uint32_t vlo,
-                                                  uint32_t vhi) {
+                                                  uint32_t kk, bool chunked, uint32_t vlo, uint32_t vhi) {
+    const InEdge ie = g.in_edge[kk];
     bool ok = true;
     if (F & F_TS) ok = in_window(ie.ts, a.t_lo, a.t_hi);  // (p,q) outside the window: no triangle through it
     // the pivot p owns CSR positions [off[p], off[p+1]): a pivot range is a position range
@@ -465,7 +452,11 @@ __device__ __forceinline__ uint32_t stage_in_edge(const GraphDev& g, const Surve
         }
         p = lo;
     }
-    uint32_t j0 = sfx.x, jend = sfx.y;
+    uint32_t j0 = ie.e + 1, jend = ie.end;
+    if (ok && g.vidx) {  // the suffix of Adj+(p) after q in the window view
+        j0 = view_pos(g.vidx, ie.e) + 1;
+        jend = view_pos(g.vidx, ie.end);
+    }
     if (ok && chunked && j0 < jend) {
         j0 = lower_bound_col(g.col, j0, jend, vlo);
         jend = upper_bound_col(g.col, j0, jend, vhi);
@@ -479,14 +470,6 @@ __device__ __forceinline__ uint32_t stage_in_edge(const GraphDev& g, const Surve
         S.e[k] = ie.e;
     }
     return (ok && j0 < jend) ? ((jend + kUnit - 1) >> kUnitLog) - (j0 >> kUnitLog) : 0u;
-}
-
-// The same from in-edge record kk of G+.
-template <int F>
-__device__ __forceinline__ uint32_t stage_in_edge(const GraphDev& g, const SurveyArgs& a, InStage S, uint32_t k,
-                                                  uint32_t kk, bool chunked, uint32_t vlo, uint32_t vhi) {
-    const InEdge ie = g.in_edge[kk];
-    return stage_in_edge<F>(g, a, S, k, ie, suffix_of<F>(g, a, ie), chunked, vlo, vhi);
 }
 
 // Last slot k in [lo, hi) with pp[k] <= f (pp non-decreasing, pp[lo] <= f).
@@ -824,12 +807,8 @@ __global__ void __launch_bounds__(kBlockThreads, CHUNK <= kBlockChunk ? 5 : 3)
             cnt = 0;
         }
         grec_prev = grec;
-        uint32_t qbase = item.qpos;
+        uint32_t qbase = (uint32_t)g.off[q] + item.qlo;
         uint32_t len = item.qlen;
-        // the first group's in-edge records and suffixes load while the out-list part is staged
-        const uint32_t n_in0 = min(kBlockInEdges, item.in_hi - item.in_lo);
-        InEdge ie0 = {};
-        if (threadIdx.x < n_in0) ie0 = g.in_edge[item.in_lo + threadIdx.x];
         if (g.vidx) {  // the item's part of Adj+(q) in the window view
             const uint32_t b0 = view_pos(g.vidx, qbase);
             len = view_pos(g.vidx, qbase + len) - b0;
@@ -839,8 +818,6 @@ __global__ void __launch_bounds__(kBlockThreads, CHUNK <= kBlockChunk ? 5 : 3)
                 continue;
             }
         }
-        uint2 sfx0 = make_uint2(0u, 0u);
-        if (threadIdx.x < n_in0) sfx0 = suffix_of<F>(g, a, ie0);
         T.size = view_table_size(len, g.vidx != nullptr, kBlockTable);
         const uint32_t tsize = T.size;
         for (uint32_t i = threadIdx.x; i < tsize; i += blockDim.x) T.key[i] = kEmpty;
@@ -853,10 +830,11 @@ __global__ void __launch_bounds__(kBlockThreads, CHUNK <= kBlockChunk ? 5 : 3)
         const uint32_t d_q = (F & F_EXTRA) ? __ldg(&g.deg[q]) : 0u;
         const uint32_t warp = threadIdx.x >> 5;
         // the table stays; the item's in-edges are staged and scanned kBlockInEdges at a time
-        uint32_t np = 0;
-        if (threadIdx.x < n_in0) np = stage_in_edge<F>(g, a, S, threadIdx.x, ie0, sfx0, chunked, vlo, vhi);
-        for (uint32_t g0 = item.in_lo;;) {
+        for (uint32_t g0 = item.in_lo; g0 < item.in_hi; g0 += kBlockInEdges) {
+            if (g0 != item.in_lo) __syncthreads();  // the previous group's stage is no longer read
             const uint32_t n_in = min(kBlockInEdges, item.in_hi - g0);
+            uint32_t np = 0;
+            if (threadIdx.x < n_in) np = stage_in_edge<F>(g, a, S, threadIdx.x, g0 + threadIdx.x, chunked, vlo, vhi);
             uint32_t total;
             const uint32_t pre = prim::block_exclusive_scan(np, scan_tmp, &total);
             if (threadIdx.x < n_in) S.pp[threadIdx.x] = pre;
@@ -865,12 +843,6 @@ __global__ void __launch_bounds__(kBlockThreads, CHUNK <= kBlockChunk ? 5 : 3)
             const uint32_t f_begin = (uint32_t)(((uint64_t)s_total * warp) / kWarps);
             const uint32_t f_end = (uint32_t)(((uint64_t)s_total * (warp + 1)) / kWarps);
             scan_flat<F>(g, a, T, S, H, n_in, f_begin, f_end, qbase, q, l_q, d_q, s_tab, grec, cnt);
-            g0 += kBlockInEdges;
-            if (g0 >= item.in_hi) break;
-            __syncthreads();  // the previous group's stage is no longer read
-            np = 0;
-            if (threadIdx.x < min(kBlockInEdges, item.in_hi - g0))
-                np = stage_in_edge<F>(g, a, S, threadIdx.x, g0 + threadIdx.x, chunked, vlo, vhi);
         }
     }
     if (grec_prev) flush_count(cnt, a, s_tab, grec_prev);
@@ -882,7 +854,6 @@ __global__ void __launch_bounds__(kBlockThreads, CHUNK <= kBlockChunk ? 5 : 3)
 
 constexpr uint32_t kWTable = kTableFactor * kWarpMaxQ;
 struct __align__(16) WarpSmem {
-    WorkItem item[2];  // the current item's record and the next one's, copied ahead
     uint32_t key[kWTable];
     uint32_t ts[kWarpMaxQ];
     uint32_t deg[kWarpMaxQ];
@@ -894,73 +865,6 @@ struct __align__(16) WarpSmem {
     uint8_t el[kWarpMaxQ];
     uint8_t vl[kWarpMaxQ];
 };
-static_assert(kWarpMaxQ <= 64 && kWarpInEdges <= 64, "a lane stages at most two entries and two in-edges");
-
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
-
-// Stage the out-list part [qbase, qbase + len) (len <= 64) in a warp's table: entries lane and
-// lane + 32, with every load issued before the first insert.
-template <int F>
-__device__ __forceinline__ void table_fill_warp(const GraphDev& g, const SurveyArgs& a, QTable<uint8_t> T,
-                                                uint32_t qbase, uint32_t len, uint32_t lane) {
-    uint32_t r[2], t[2], el[2], vl[2], dg[2];
-    bool in[2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const uint32_t i = lane + 32u * h;
-        in[h] = i < len;
-        r[h] = in[h] ? __ldg(&g.col[qbase + i]) : 0u;
-        t[h] = ((F & F_TS) && in[h]) ? __ldg(&g.ts[qbase + i]) : 0u;
-        el[h] = ((F & F_EL) && in[h]) ? __ldg(&g.el[qbase + i]) : 0u;
-    }
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        // entries outside the window can close no surveyed triangle
-        if (F & F_TS) in[h] = in[h] && in_window(t[h], a.t_lo, a.t_hi);
-        vl[h] = ((F & F_VL) && in[h]) ? __ldg(&g.vl[r[h]]) : 0u;
-        dg[h] = ((F & F_EXTRA) && in[h]) ? __ldg(&g.deg[r[h]]) : 0u;
-    }
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        if (!in[h]) continue;
-        const uint32_t i = lane + 32u * h;
-        uint32_t slot = hash_slot(r[h], T.size);
-        while (atomicCAS(&T.key[slot], kEmpty, r[h]) != kEmpty)
-            if (++slot == T.size) slot = 0;
-        T.pos[slot] = (uint8_t)i;
-        if (F & F_TS) T.ts[i] = t[h];
-        if (F & F_EL) T.el[i] = (uint8_t)el[h];
-        if (F & F_VL) T.vl[i] = (uint8_t)vl[h];
-        if (F & F_EXTRA) T.deg[i] = dg[h];
-    }
-}
-
-// Prefix of the unit counts of in-edge slots (lane, lane + 32) into pp, then the warp's scan of the
-// item's units.
-template <int F>
-__device__ __forceinline__ void scan_warp_item(uint32_t np0, uint32_t np1, uint32_t n_in, WarpSmem& ws,
-                                               const GraphDev& g, const SurveyArgs& a, const QTable<uint8_t>& T,
-                                               const InStage& S, uint32_t qbase, uint32_t q, uint32_t l_q,
-                                               uint32_t d_q, MirrorWord* s_tab, unsigned long long* grec,
-                                               unsigned long long& cnt) {
-    const uint32_t lane = threadIdx.x & 31;
-    uint32_t x0 = np0, x1 = np1;
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y0 = __shfl_up_sync(0xffffffffu, x0, o), y1 = __shfl_up_sync(0xffffffffu, x1, o);
-        if (lane >= (uint32_t)o) { x0 += y0; x1 += y1; }
-    }
-    const uint32_t half = __shfl_sync(0xffffffffu, x0, 31);
-    const uint32_t total = half + __shfl_sync(0xffffffffu, x1, 31);
-    if (lane < n_in) ws.pp[lane] = x0 - np0;
-    if (lane + 32 < n_in) ws.pp[lane + 32] = half + x1 - np1;
-    if (lane == 0) ws.pp[n_in] = total;
-    __syncwarp();
-    HitQueue H;
-    H.idx = ws.qidx;
-    H.pk = ws.qpk;
-    scan_flat<F>(g, a, T, S, H, n_in, 0, total, qbase, q, l_q, d_q, s_tab, grec, cnt);
-}
 
 // 5 resident blocks per SM, like the block kernel (the register cap that sets)
 template <int F>
@@ -969,7 +873,7 @@ __global__ void __launch_bounds__(kBlockThreads, 5) survey_warp_kernel(GraphDev 
     extern __shared__ __align__(16) unsigned char smem[];
     MirrorWord* s_tab = reinterpret_cast<MirrorWord*>(smem + multi_bytes<F>());
     WarpSmem* ws_all = reinterpret_cast<WarpSmem*>(smem + multi_bytes<F>() + mirror_bytes<F>(a.s_words));
-    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpSmem& ws = ws_all[warp];
     init_shared<F>(s_tab, a.s_words, a.counters);
     __syncthreads();
@@ -981,27 +885,13 @@ __global__ void __launch_bounds__(kBlockThreads, 5) survey_warp_kernel(GraphDev 
     unsigned long long* grec_prev = nullptr;
     uint32_t taken = 0;  // items this warp has taken (warp-uniform)
 
-    // Items are dealt round-robin -- warp w of W takes items w, w + W, ... (a fair sample of the item
-    // sizes for every warp) -- so the next item is known in advance, and its record is copied into
-    // shared memory while the current one is surveyed.
-    // (The buffer of item k of a warp is k & 1; fields are read from shared memory where they are
-    // used, which keeps them out of registers.)
-    uint32_t it = blockIdx.x * kWarps + warp;
-    if (it < n_items && lane < 2)
-        prim::cp_async16(reinterpret_cast<char*>(&ws.item[0]) + 16 * lane,
-                         reinterpret_cast<const char*>(items + it) + 16 * lane, 16);
-    cp_async_commit();
-    for (; it < n_items; it += gridDim.x * kWarps) {
-        cp_async_wait_all();
-        __syncwarp();  // the record is visible to the warp; the other buffer's record was read by all lanes
-        const uint32_t buf = taken & 1u;
-        const WorkItem& item = ws.item[buf];
-        const uint32_t next = it + gridDim.x * kWarps;
-        if (next < n_items && lane < 2)
-            prim::cp_async16(reinterpret_cast<char*>(&ws.item[buf ^ 1u]) + 16 * lane,
-                             reinterpret_cast<const char*>(items + next) + 16 * lane, 16);
-        cp_async_commit();
+    while (true) {
+        uint32_t it = 0;
+        if (lane == 0) it = atomicAdd(&a.counters[0], 1u);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= n_items) break;
         if ((++taken & ((1u << a.move_warp_log2) - 1u)) == 0) move_mirror_warp<F>(s_tab, a.s_words, a.out);
+        const WorkItem item = items[it];
         const uint32_t q = item.q;
         unsigned long long* grec = record_of(g, a, q);
         if (grec != grec_prev && grec_prev) {
@@ -1009,13 +899,8 @@ __global__ void __launch_bounds__(kBlockThreads, 5) survey_warp_kernel(GraphDev 
             cnt = 0;
         }
         grec_prev = grec;
-        uint32_t qbase = item.qpos;
+        uint32_t qbase = (uint32_t)g.off[q];
         uint32_t len = item.qlen;
-        const uint32_t n_in = item.in_hi - item.in_lo;
-        // the in-edge records load while Adj+(q) is translated and staged
-        InEdge ie0 = {}, ie1 = {};
-        if (lane < n_in) ie0 = g.in_edge[item.in_lo + lane];
-        if (lane + 32 < n_in) ie1 = g.in_edge[item.in_lo + lane + 32];
         if (g.vidx) {  // Adj+(q) in the window view
             const uint32_t b0 = view_pos(g.vidx, qbase);
             len = view_pos(g.vidx, qbase + len) - b0;
@@ -1024,38 +909,40 @@ __global__ void __launch_bounds__(kBlockThreads, 5) survey_warp_kernel(GraphDev 
         }
         const uint32_t l_q = (F & F_VL) ? __ldg(&g.vl[q]) : 0u;
         const uint32_t d_q = (F & F_EXTRA) ? __ldg(&g.deg[q]) : 0u;
-        uint32_t np0 = 0, np1 = 0;
-        if (len <= kWarpMaxQ) {  // one part: the whole list, every in-edge's whole suffix
-            uint2 sfx0 = make_uint2(0u, 0u), sfx1 = make_uint2(0u, 0u);
-            if (lane < n_in) sfx0 = suffix_of<F>(g, a, ie0);
-            if (lane + 32 < n_in) sfx1 = suffix_of<F>(g, a, ie1);
-            T.size = view_table_size(len, g.vidx != nullptr, kWTable);
+        const uint32_t n_in = item.in_hi - item.in_lo;
+        const bool chunked = len > kWarpMaxQ;
+        // the out-list is staged kWarpMaxQ entries at a time (one part unless the window
+        // leaves more in it); each part restricts the suffixes to its value range
+        for (uint32_t c0 = 0; c0 < len; c0 += kWarpMaxQ) {
+            const uint32_t clen = min(kWarpMaxQ, len - c0);
+            T.size = view_table_size(clen, g.vidx != nullptr, kWTable);
             const uint32_t tsize = T.size;
             __syncwarp();
             for (uint32_t i = lane; i < tsize; i += 32) ws.key[i] = kEmpty;
-            if (lane < n_in) np0 = stage_in_edge<F>(g, a, S, lane, ie0, sfx0, false, 0u, 0xFFFFFFFFu);
-            if (lane + 32 < n_in) np1 = stage_in_edge<F>(g, a, S, lane + 32, ie1, sfx1, false, 0u, 0xFFFFFFFFu);
             __syncwarp();
-            table_fill_warp<F>(g, a, T, qbase, len, lane);
-        }
-        // several parts (a window view leaves more than kWarpMaxQ entries) are staged kWarpMaxQ at a
-        // time, each restricting the suffixes to its value range
-        for (uint32_t c0 = 0; c0 < len; c0 += kWarpMaxQ) {
-            if (len > kWarpMaxQ) {
-                const uint32_t clen = min(kWarpMaxQ, len - c0);
-                T.size = view_table_size(clen, g.vidx != nullptr, kWTable);
-                const uint32_t tsize = T.size;
-                __syncwarp();
-                for (uint32_t i = lane; i < tsize; i += 32) ws.key[i] = kEmpty;
-                __syncwarp();
-                table_fill<F>(g, a, T, qbase + c0, clen, lane, 32);
-                const uint32_t vlo = __ldg(&g.col[qbase + c0]);
-                const uint32_t vhi = __ldg(&g.col[qbase + c0 + clen - 1]);
-                np0 = lane < n_in ? stage_in_edge<F>(g, a, S, lane, item.in_lo + lane, true, vlo, vhi) : 0u;
-                np1 = lane + 32 < n_in ? stage_in_edge<F>(g, a, S, lane + 32, item.in_lo + lane + 32, true, vlo, vhi)
-                                       : 0u;
+            table_fill<F>(g, a, T, qbase + c0, clen, lane, 32);
+            const uint32_t vlo = chunked ? __ldg(&g.col[qbase + c0]) : 0u;
+            const uint32_t vhi = chunked ? __ldg(&g.col[qbase + c0 + clen - 1]) : 0xFFFFFFFFu;
+            uint32_t np0 = 0, np1 = 0;
+            if ((uint32_t)lane < n_in) np0 = stage_in_edge<F>(g, a, S, lane, item.in_lo + lane, chunked, vlo, vhi);
+            if ((uint32_t)lane + 32 < n_in)
+                np1 = stage_in_edge<F>(g, a, S, lane + 32, item.in_lo + lane + 32, chunked, vlo, vhi);
+            // exclusive prefix over slots 0..63 held as (lane, lane + 32)
+            uint32_t x0 = np0, x1 = np1;
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y0 = __shfl_up_sync(0xffffffffu, x0, o), y1 = __shfl_up_sync(0xffffffffu, x1, o);
+                if (lane >= o) { x0 += y0; x1 += y1; }
             }
-            scan_warp_item<F>(np0, np1, n_in, ws, g, a, T, S, qbase + c0, q, l_q, d_q, s_tab, grec, cnt);
+            const uint32_t half = __shfl_sync(0xffffffffu, x0, 31);
+            const uint32_t total = half + __shfl_sync(0xffffffffu, x1, 31);
+            if ((uint32_t)lane < n_in) ws.pp[lane] = x0 - np0;
+            if ((uint32_t)lane + 32 < n_in) ws.pp[lane + 32] = half + x1 - np1;
+            if (lane == 0) ws.pp[n_in] = total;
+            __syncwarp();
+            HitQueue H;
+            H.idx = ws.qidx;
+            H.pk = ws.qpk;
+            scan_flat<F>(g, a, T, S, H, n_in, 0, total, qbase + c0, q, l_q, d_q, s_tab, grec, cnt);
         }
     }
     if (grec_prev) flush_count(cnt, a, s_tab, grec_prev);
