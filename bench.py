@@ -660,23 +660,32 @@ def run_serve(args):
         assert np.array_equal(o, want), "served result differs from the request alone"
     served_s = time.perf_counter() - t0
     burst_stats = tp.tripoll_server_stats(srv)
-    # Poisson arrivals at a fraction of the served capacity -> latency under load
-    rate = args.load * R / served_s
-    gaps = [-np.log(1.0 - ((synth.draw(7, 2, i) >> 11) * 2.0 ** -53)) / rate for i in range(R)]
-    ids = []
-    t0 = time.perf_counter()
-    t_next = t0
-    for (gi, k, lo, hi), gap in zip(reqs, gaps):
-        t_next += gap
-        while time.perf_counter() < t_next:
-            pass
-        ids.append(tp.tripoll_server_submit(srv, slots[gi], k, lo, hi))
-    lat_poisson = []
-    for rid, w in zip(ids, words):
-        o = np.zeros(w, np.uint64)
-        lat_poisson.append(tp.tripoll_server_wait(srv, rid, o, 600000) * 1e-9)
-    all_stats = tp.tripoll_server_stats(srv)
-    poisson_stats = {k: all_stats[k] - burst_stats[k] for k in all_stats}
+    # Poisson arrivals at fractions of the served capacity -> latency under load
+    def poisson(load, stream):
+        rate = load * R / served_s
+        gaps = [-np.log(1.0 - ((synth.draw(7, stream, i) >> 11) * 2.0 ** -53)) / rate for i in range(R)]
+        before = tp.tripoll_server_stats(srv)
+        ids = []
+        t_next = time.perf_counter()
+        for (gi, k, lo, hi), gap in zip(reqs, gaps):
+            t_next += gap
+            while time.perf_counter() < t_next:
+                pass
+            ids.append(tp.tripoll_server_submit(srv, slots[gi], k, lo, hi))
+        lat = []
+        for rid, w in zip(ids, words):
+            o = np.zeros(w, np.uint64)
+            lat.append(tp.tripoll_server_wait(srv, rid, o, 600000) * 1e-9)
+        after = tp.tripoll_server_stats(srv)
+        return rate, lat, {k: after[k] - before[k] for k in after}
+
+    loads = [float(x) for x in args.loads.split(",")] if args.loads else []
+    if args.load not in loads:
+        loads.append(args.load)
+    sweep = []
+    for j, load in enumerate(sorted(loads)):
+        rate, lat, st = poisson(load, 2 + j)
+        sweep.append({"load": load, "rate_per_s": rate, "lat": lat, "server": st})
     tp.tripoll_server_destroy(srv)
     for h in handles:
         tp.tripoll_destroy(h)
@@ -696,8 +705,11 @@ def run_serve(args):
         "plain_path": {"requests_per_s": R / plain_s, "p50_ms": pct(lat_plain, 50), "p99_ms": pct(lat_plain, 99)},
         "served_burst": {"requests_per_s": R / served_s, "p50_ms": pct(lat_burst, 50), "p99_ms": pct(lat_burst, 99),
                          "server": burst_stats},
-        "served_poisson": {"rate_per_s": rate, "p50_ms": pct(lat_poisson, 50), "p99_ms": pct(lat_poisson, 99),
-                           "server": poisson_stats},
+        "served_poisson": next({"load": r["load"], "rate_per_s": r["rate_per_s"], "p50_ms": pct(r["lat"], 50),
+                                "p99_ms": pct(r["lat"], 99), "server": r["server"]}
+                               for r in sweep if r["load"] == args.load),
+        "served_poisson_sweep": [{"load": r["load"], "rate_per_s": r["rate_per_s"], "p50_ms": pct(r["lat"], 50),
+                                  "p99_ms": pct(r["lat"], 99)} for r in sweep],
         "served_over_plain": plain_s / served_s,
     }
 
@@ -730,6 +742,8 @@ def main():
     ap.add_argument("--scratch-gb", type=int, default=40)
     ap.add_argument("--max-inflight", type=int, default=32)
     ap.add_argument("--load", type=float, default=0.7)
+    ap.add_argument("--loads", default="0.3,0.5,0.9",
+                    help="serve: further Poisson loads (fractions of the served capacity) for the latency sweep")
     args = ap.parse_args()
     if args.impl != "reference":
         _ensure_built()
