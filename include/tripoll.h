@@ -185,8 +185,9 @@ uint64_t tripoll_result_words(uint32_t kind_mask, uint32_t num_vlabels, uint32_t
 /* Run one survey (Alg. 1 with the fold of the requested kinds) over every
  * triangle of g whose edge timestamps lie in [t_lo, t_hi].  A window other
  * than [0, 0xFFFFFFFF] first compacts G+ to its in-window edges (about
- * 13 bytes per edge of stream-ordered pool memory, released when the survey
- * ends), so that wedges through an out-of-window edge are never checked.
+ * 10 bytes per edge of stream-ordered pool memory, 14 with per-edge counts,
+ * released when the survey ends), so that wedges through an out-of-window
+ * edge are never checked.
  *   result  device or host, uint64[tripoll_result_words(kinds, ...)]; overwritten.
  *           For a batched graph: uint64[num_graphs * words], graph i's tables
  *           at offset i * words.
