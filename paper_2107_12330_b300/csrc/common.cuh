@@ -130,6 +130,12 @@ struct GraphDev {
     // through vidx.  (8 bytes per 32 edges: the index stays in L2 on large graphs.)
     const uint2* vidx = nullptr;        // [(m >> 5) + 1] or null
     const uint32_t* vorig = nullptr;    // [m] CSR position in G+ of each view entry (per-edge counts only)
+    // The window view's in-edges: when set, in_edge above holds only the in-edge records whose edge lies in
+    // the window (same order), with e and end already positions of the view, iidx tells where in-edge
+    // record k of G+ lands among them (as vidx does for CSR positions), and vin_e gives the CSR position in
+    // G+ of each one's edge (p,q).  Work items keep G+'s in-edge ranges and are translated through iidx.
+    const uint2* iidx = nullptr;        // [(m >> 5) + 1] or null
+    const uint32_t* vin_e = nullptr;    // [in-window in-edges]
 };
 
 }  // namespace tp

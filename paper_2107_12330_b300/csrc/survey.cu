@@ -198,6 +198,44 @@ __global__ void window_view_kernel(const uint32_t* __restrict__ col, const uint3
     }
 }
 
+// The view's in-edges, first part: per 32 in-edge records, the in-window bits (into iidx[w].y) and
+// their count (the input of the scan that gives iidx[w].x).
+__global__ void in_view_bits_kernel(const InEdge* __restrict__ in_edge, uint64_t m, uint64_t words, uint32_t lo,
+                                    uint32_t hi, uint2* __restrict__ iidx, uint32_t* __restrict__ cnt) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;  // a multiple of 32: warps stay aligned
+    for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < words * 32; k += stride) {
+        bool in = false;
+        if (k < m) {
+            const uint32_t t = in_edge[k].ts;
+            in = t >= lo && t <= hi;
+        }
+        const unsigned bits = __ballot_sync(0xffffffffu, in);
+        if ((threadIdx.x & 31) == 0) {
+            iidx[k >> 5].y = bits;
+            cnt[k >> 5] = __popc(bits);
+        }
+    }
+}
+
+// ... then the in-window records, in order, with e and end translated into the view's positions, and (for
+// pivot ranges and the kinds that need it) the G+ position of each one's edge.
+__global__ void in_view_kernel(const InEdge* __restrict__ in_edge, const uint2* __restrict__ iidx,
+                               const uint2* __restrict__ vidx, uint64_t m, uint32_t lo, uint32_t hi,
+                               InEdge* __restrict__ vin, uint32_t* __restrict__ vin_e) {
+    for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < m; k += (uint64_t)gridDim.x * blockDim.x) {
+        const InEdge ie = in_edge[k];
+        if (ie.ts < lo || ie.ts > hi) continue;
+        const uint32_t at = view_pos(iidx, (uint32_t)k);
+        InEdge v;
+        v.e = view_pos(vidx, ie.e);
+        v.end = view_pos(vidx, ie.end);
+        v.ts = ie.ts;
+        v.meta = ie.meta;
+        vin[at] = v;
+        if (vin_e) vin_e[at] = ie.e;
+    }
+}
+
 uint64_t view_words(uint64_t m) { return (m >> 5) + 1; }
 size_t window_scan_bytes(uint64_t m) { return prim::scan_scratch_bytes(view_words(m)); }
 constexpr LaunchFn kLaunch[64] = {
@@ -303,8 +341,9 @@ uint64_t window_view_bytes(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo
     const uint64_t m = g->m;
     const uint64_t r = 256;  // pool rounding per allocation
     const uint64_t w = view_words(m);
-    return (w * 8 + r) + 2 * (w * 4 + r) + 2 * ((m + kColPad) * 4 + r) + (g->el ? m + kColPad + r : 0) +
-           ((kinds & TRIPOLL_EDGE_LOCAL) ? m * 4 + r : 0) + window_scan_bytes(m) + r;
+    return 2 * (w * 8 + r) + 2 * (w * 4 + r) + 2 * ((m + kColPad) * 4 + r) + (g->el ? m + kColPad + r : 0) +
+           (m * sizeof(InEdge) + r) + (m * 4 + r) + ((kinds & TRIPOLL_EDGE_LOCAL) ? m * 4 + r : 0) +
+           window_scan_bytes(m) + r;
 }
 
 // Launch the survey kernels accumulating into `acc` (zeroed by the caller).
@@ -382,7 +421,7 @@ int launch_survey(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_
     }
     mark(ev, 0, s);
     GraphDev gd = g->dev();
-    Scratch vx, vcnt, vpre, vcol, vts, vel, vorig, vtmp;  // released (stream-ordered) after the survey kernels
+    Scratch vx, vcnt, vpre, vcol, vts, vel, vorig, vtmp, ix, vin, vine;  // released (stream-ordered) after the kernels
     if (window && window_view && g->m) {
         const uint64_t m = g->m, words = view_words(m);
         TP_CUDA(vx.alloc(words * 8, s));
@@ -405,11 +444,28 @@ int launch_survey(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_
                                                      g->el ? vel.as<uint8_t>() : nullptr,
                                                      vorig.as<uint32_t>()); ::tp::note_launch();
         TP_CUDA(cudaGetLastError());
+        // the in-edges in the window, their positions in the view (the counts and the scan reuse vcnt and vpre)
+        TP_CUDA(ix.alloc(words * 8, s));
+        TP_CUDA(vin.alloc(m * sizeof(InEdge), s));
+        const bool need_e = a.restricted || (F & F_EXTRA);  // the kernels read vin_e only then
+        if (need_e) TP_CUDA(vine.alloc(m * 4, s));
+        in_view_bits_kernel<<<grid_n(words * 32), 256, 0, s>>>(g->in_edge, m, words, t_lo, t_hi, ix.as<uint2>(),
+                                                               vcnt.as<uint32_t>()); ::tp::note_launch();
+        if ((rc = prim::scan<uint32_t, false>(prim::Load<uint32_t, uint32_t>{vcnt.as<uint32_t>(), words},
+                                              vpre.as<uint32_t>(), words, vtmp.ptr, s)))
+            return rc;
+        view_prefix_kernel<<<grid_n(words), 256, 0, s>>>(vpre.as<uint32_t>(), words, ix.as<uint2>()); ::tp::note_launch();
+        in_view_kernel<<<grid_n(m), 256, 0, s>>>(g->in_edge, ix.as<uint2>(), vx.as<uint2>(), m, t_lo, t_hi,
+                                                 vin.as<InEdge>(), need_e ? vine.as<uint32_t>() : nullptr); ::tp::note_launch();
+        TP_CUDA(cudaGetLastError());
         gd.col = vcol.as<uint32_t>();
         gd.ts = vts.as<uint32_t>();
         gd.el = g->el ? vel.as<uint8_t>() : nullptr;
         gd.vidx = vx.as<uint2>();
         gd.vorig = vorig.as<uint32_t>();
+        gd.in_edge = vin.as<InEdge>();
+        gd.iidx = ix.as<uint2>();
+        gd.vin_e = need_e ? vine.as<uint32_t>() : nullptr;
     }
     kLaunch[F](g, gd, a, s, sms, ev);
     TP_CUDA(cudaGetLastError());

@@ -440,20 +440,23 @@ __device__ __forceinline__ uint32_t stage_in_edge(const GraphDev& g, const Surve
                                                   uint32_t kk, bool chunked, uint32_t vlo, uint32_t vhi) {
     const InEdge ie = g.in_edge[kk];
     bool ok = true;
-    if (F & F_TS) ok = in_window(ie.ts, a.t_lo, a.t_hi);  // (p,q) outside the window: no triangle through it
+    // (p,q) outside the window: no triangle through it (the view's in-edges are all inside)
+    if ((F & F_TS) && !g.iidx) ok = in_window(ie.ts, a.t_lo, a.t_hi);
+    // the CSR position of (p,q) in G+
+    const uint32_t eg = (g.iidx && (a.restricted || (F & F_EXTRA))) ? __ldg(&g.vin_e[kk]) : ie.e;
     // the pivot p owns CSR positions [off[p], off[p+1]): a pivot range is a position range
-    if (a.restricted && (ie.e < a.e_lo || ie.e >= a.e_hi)) ok = false;
+    if (a.restricted && (eg < a.e_lo || eg >= a.e_hi)) ok = false;
     uint32_t p = 0;
     if (F & F_EXTRA) {  // p itself: the last vertex whose out-list starts at or before e
         uint32_t lo = 0, hi = (uint32_t)g.n - 1;
         while (lo < hi) {
             const uint32_t mid = lo + ((hi - lo + 1) >> 1);
-            if (__ldg(&g.off[mid]) <= ie.e) lo = mid; else hi = mid - 1;
+            if (__ldg(&g.off[mid]) <= eg) lo = mid; else hi = mid - 1;
         }
         p = lo;
     }
-    uint32_t j0 = ie.e + 1, jend = ie.end;
-    if (ok && g.vidx) {  // the suffix of Adj+(p) after q in the window view
+    uint32_t j0 = ie.e + 1, jend = ie.end;  // (a view in-edge record holds view positions already)
+    if (ok && g.vidx && !g.iidx) {  // the suffix of Adj+(p) after q in the window view
         j0 = view_pos(g.vidx, ie.e) + 1;
         jend = view_pos(g.vidx, ie.end);
     }
@@ -467,7 +470,7 @@ __device__ __forceinline__ uint32_t stage_in_edge(const GraphDev& g, const Surve
     S.meta[k] = ie.meta;
     if (F & F_EXTRA) {
         S.p[k] = p;
-        S.e[k] = ie.e;
+        S.e[k] = eg;
     }
     return (ok && j0 < jend) ? ((jend + kUnit - 1) >> kUnitLog) - (j0 >> kUnitLog) : 0u;
 }
@@ -809,12 +812,17 @@ __global__ void __launch_bounds__(kBlockThreads, CHUNK <= kBlockChunk ? 5 : 3)
         grec_prev = grec;
         uint32_t qbase = (uint32_t)g.off[q] + item.qlo;
         uint32_t len = item.qlen;
+        uint32_t in_lo = item.in_lo, in_hi = item.in_hi;
         if (g.vidx) {  // the item's part of Adj+(q) in the window view
             const uint32_t b0 = view_pos(g.vidx, qbase);
             len = view_pos(g.vidx, qbase + len) - b0;
             qbase = b0;
-            if (len == 0) {  // no in-window (q,r): no triangle; s_item is read by all before it changes
-                __syncthreads();
+            if (g.iidx) {  // and its in-window in-edges
+                in_lo = view_pos(g.iidx, in_lo);
+                in_hi = view_pos(g.iidx, in_hi);
+            }
+            if (len == 0 || in_lo == in_hi) {  // no in-window (q,r) or (p,q): no triangle; s_item is read by
+                __syncthreads();                // all before it changes
                 continue;
             }
         }
@@ -830,9 +838,9 @@ __global__ void __launch_bounds__(kBlockThreads, CHUNK <= kBlockChunk ? 5 : 3)
         const uint32_t d_q = (F & F_EXTRA) ? __ldg(&g.deg[q]) : 0u;
         const uint32_t warp = threadIdx.x >> 5;
         // the table stays; the item's in-edges are staged and scanned kBlockInEdges at a time
-        for (uint32_t g0 = item.in_lo; g0 < item.in_hi; g0 += kBlockInEdges) {
-            if (g0 != item.in_lo) __syncthreads();  // the previous group's stage is no longer read
-            const uint32_t n_in = min(kBlockInEdges, item.in_hi - g0);
+        for (uint32_t g0 = in_lo; g0 < in_hi; g0 += kBlockInEdges) {
+            if (g0 != in_lo) __syncthreads();  // the previous group's stage is no longer read
+            const uint32_t n_in = min(kBlockInEdges, in_hi - g0);
             uint32_t np = 0;
             if (threadIdx.x < n_in) np = stage_in_edge<F>(g, a, S, threadIdx.x, g0 + threadIdx.x, chunked, vlo, vhi);
             uint32_t total;
@@ -901,15 +909,20 @@ __global__ void __launch_bounds__(kBlockThreads, 5) survey_warp_kernel(GraphDev 
         grec_prev = grec;
         uint32_t qbase = (uint32_t)g.off[q];
         uint32_t len = item.qlen;
+        uint32_t in_lo = item.in_lo, in_hi = item.in_hi;
         if (g.vidx) {  // Adj+(q) in the window view
             const uint32_t b0 = view_pos(g.vidx, qbase);
             len = view_pos(g.vidx, qbase + len) - b0;
             qbase = b0;
-            if (len == 0) continue;  // no in-window (q,r): no triangle
+            if (g.iidx) {  // and its in-window in-edges
+                in_lo = view_pos(g.iidx, in_lo);
+                in_hi = view_pos(g.iidx, in_hi);
+            }
+            if (len == 0 || in_lo == in_hi) continue;  // no in-window (q,r) or (p,q): no triangle
         }
         const uint32_t l_q = (F & F_VL) ? __ldg(&g.vl[q]) : 0u;
         const uint32_t d_q = (F & F_EXTRA) ? __ldg(&g.deg[q]) : 0u;
-        const uint32_t n_in = item.in_hi - item.in_lo;
+        const uint32_t n_in = in_hi - in_lo;
         const bool chunked = len > kWarpMaxQ;
         // the out-list is staged kWarpMaxQ entries at a time (one part unless the window
         // leaves more in it); each part restricts the suffixes to its value range
@@ -924,9 +937,9 @@ __global__ void __launch_bounds__(kBlockThreads, 5) survey_warp_kernel(GraphDev 
             const uint32_t vlo = chunked ? __ldg(&g.col[qbase + c0]) : 0u;
             const uint32_t vhi = chunked ? __ldg(&g.col[qbase + c0 + clen - 1]) : 0xFFFFFFFFu;
             uint32_t np0 = 0, np1 = 0;
-            if ((uint32_t)lane < n_in) np0 = stage_in_edge<F>(g, a, S, lane, item.in_lo + lane, chunked, vlo, vhi);
+            if ((uint32_t)lane < n_in) np0 = stage_in_edge<F>(g, a, S, lane, in_lo + lane, chunked, vlo, vhi);
             if ((uint32_t)lane + 32 < n_in)
-                np1 = stage_in_edge<F>(g, a, S, lane + 32, item.in_lo + lane + 32, chunked, vlo, vhi);
+                np1 = stage_in_edge<F>(g, a, S, lane + 32, in_lo + lane + 32, chunked, vlo, vhi);
             // exclusive prefix over slots 0..63 held as (lane, lane + 32)
             uint32_t x0 = np0, x1 = np1;
             for (int o = 1; o < 32; o <<= 1) {
