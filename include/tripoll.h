@@ -184,16 +184,18 @@ uint64_t tripoll_result_words(uint32_t kind_mask, uint32_t num_vlabels, uint32_t
 
 /* Run one survey (Alg. 1 with the fold of the requested kinds) over every
  * triangle of g whose edge timestamps lie in [t_lo, t_hi].  A window other
- * than [0, 0xFFFFFFFF] first compacts G+ to its in-window edges (about
- * 10 bytes per edge of stream-ordered pool memory, 14 with per-edge counts,
- * released when the survey ends), so that wedges through an out-of-window
- * edge are never checked.
+ * than [0, 0xFFFFFFFF] first compacts G+ and its in-edge records to the
+ * in-window edges (about 26 bytes per in-window edge of stream-ordered pool
+ * memory, 30 with per-edge counts, and 0.75 per edge of G+, released when
+ * the survey ends), so that wedges through an out-of-window edge are never
+ * checked.  Sizing that view reads the in-window edge count back: the call
+ * then waits for cuda_stream's earlier work and the view's first kernels.
  *   result  device or host, uint64[tripoll_result_words(kinds, ...)]; overwritten.
  *           For a batched graph: uint64[num_graphs * words], graph i's tables
  *           at offset i * words.
  *   Errors: INVALID_ARG (t_lo > t_hi, kind_mask == 0 or unknown bits),
- *   NO_EDGE_LABELS, NO_MEMORY, CUDA.  Asynchronous for a device result;
- *   synchronises cuda_stream for a host result. */
+ *   NO_EDGE_LABELS, NO_MEMORY, CUDA.  Asynchronous for a device result
+ *   (apart from that wait); synchronises cuda_stream for a host result. */
 int tripoll_survey(tripoll_graph_t g, uint32_t kind_mask, uint32_t t_lo, uint32_t t_hi,
                    uint64_t* result, void* cuda_stream);
 
@@ -343,7 +345,11 @@ void tripoll_destroy(tripoll_graph_t g);
  * requests on batched graphs, run one per batch. */
 int tripoll_server_create(uint64_t scratch_cap_bytes, uint32_t max_inflight,
                           tripoll_server_t* out);
-/* Make g resident in the server (the server does not take ownership). */
+/* Make g resident in the server (the server does not take ownership).  The
+ * first time a graph is added, a histogram of its timestamps is taken (a few
+ * kernels on the current device, which must be g's, and a read-back; the
+ * call synchronises) so that a request is charged the window view of the
+ * edges its window can hold rather than of all of them. */
 int tripoll_server_add_graph(tripoll_server_t s, tripoll_graph_t g, uint32_t* slot);
 /* Queue a request; returns its id.  Thread-safe. */
 int tripoll_server_submit(tripoll_server_t s, uint32_t slot, uint32_t kind_mask, uint32_t t_lo,

@@ -165,6 +165,10 @@ struct tripoll_graph {
     tp::WorkItem* items_warp = nullptr;   // d+(q) <= plan.warp_max_dplus
     tp::WorkItem* items_block = nullptr;  // up to plan.long_list_min_dplus, parts of kBlockChunk
     tp::WorkItem* items_big = nullptr;    // longer out-lists, parts of kBigChunk
+    // Edges by timestamp bucket (bucket b holds the timestamps t with t >> ts_shift == b), which bounds on the
+    // host how many edges a window holds; filled on demand (tp::ts_histogram), empty until then.
+    std::vector<uint64_t> ts_hist;
+    uint32_t ts_shift = 0;
     uint64_t n_items_warp = 0, n_items_block = 0, n_items_big = 0;
     // statistics
     tripoll_graph_info info{};
@@ -240,6 +244,9 @@ uint64_t survey_many_bytes(const tripoll_graph* g, uint32_t count, const uint32_
                            const uint32_t* t_hi, bool window_view);
 // Device scratch the window view of g takes for [t_lo, t_hi] (0 for the full window).
 uint64_t window_view_bytes(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_t t_hi);
+// Fill g->ts_hist (a few kernels over the timestamps, then a read-back; synchronises) unless it is filled
+// already or g lives on another device than the current one (then window_view_bytes bounds by |E+|).
+int ts_histogram(tripoll_graph* g);
 // Allocate count elements of T for graph g on stream s (recorded in g->blocks).
 template <class T> cudaError_t galloc(tripoll_graph* g, T** p, uint64_t count, cudaStream_t s) {
     Block b;

@@ -312,6 +312,8 @@ extern "C" int tripoll_server_create(uint64_t scratch_cap_bytes, uint32_t max_in
 
 extern "C" int tripoll_server_add_graph(tripoll_server_t s, tripoll_graph_t g, uint32_t* slot) {
     if (!s || !g || !slot) return fail(TRIPOLL_ERR_INVALID_ARG, "NULL argument");
+    // the timestamp histogram that bounds each request's window view for the scratch budget
+    if (int rc = ts_histogram(g)) return rc;
     std::lock_guard<std::mutex> lk(s->mu);
     s->graphs.push_back(g);
     *slot = (uint32_t)(s->graphs.size() - 1);

@@ -336,14 +336,83 @@ int build_plan(tripoll_graph* g, cudaStream_t s) {
     return TRIPOLL_OK;
 }
 
+// Pool memory of a survey's window view: the two indexes and scan buffers by |E+|, the compacted arrays by
+// the in-window edges -- bounded by the timestamp histogram when the graph has one, else by |E+|.
 uint64_t window_view_bytes(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_t t_hi) {
     if ((t_lo == 0 && t_hi == 0xFFFFFFFFu) || !g->m) return 0;
     const uint64_t m = g->m;
+    uint64_t mv = m;
+    if (!g->ts_hist.empty()) {
+        mv = 0;
+        const uint64_t b0 = t_lo >> g->ts_shift, b1 = std::min<uint64_t>(t_hi >> g->ts_shift, g->ts_hist.size() - 1);
+        for (uint64_t b = b0; b <= b1 && b < g->ts_hist.size(); ++b) mv += g->ts_hist[b];
+    }
     const uint64_t r = 256;  // pool rounding per allocation
     const uint64_t w = view_words(m);
-    return 2 * (w * 8 + r) + 2 * (w * 4 + r) + 2 * ((m + kColPad) * 4 + r) + (g->el ? m + kColPad + r : 0) +
-           (m * sizeof(InEdge) + r) + (m * 4 + r) + ((kinds & TRIPOLL_EDGE_LOCAL) ? m * 4 + r : 0) +
-           window_scan_bytes(m) + r;
+    return 2 * (w * 8 + r) + 2 * (w * 4 + r) + window_scan_bytes(m) + r + 2 * ((mv + kColPad) * 4 + r) +
+           (g->el ? mv + kColPad + r : 0) + (std::max<uint64_t>(mv, 1) * sizeof(InEdge) + r) +
+           (std::max<uint64_t>(mv, 1) * 4 + r) + ((kinds & TRIPOLL_EDGE_LOCAL) ? std::max<uint64_t>(mv, 1) * 4 + r : 0);
+}
+
+namespace {
+constexpr uint32_t kTsBuckets = 4096;
+
+__global__ void ts_max_kernel(const uint32_t* __restrict__ ts, uint64_t m, unsigned* __restrict__ out) {
+    unsigned v = 0;
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < m; e += (uint64_t)gridDim.x * blockDim.x)
+        v = max(v, ts[e]);
+    for (int o = 16; o; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, v);
+}
+
+__global__ void ts_hist_kernel(const uint32_t* __restrict__ ts, uint64_t m, uint32_t shift,
+                               unsigned long long* __restrict__ hist) {
+    __shared__ uint32_t h[kTsBuckets];
+    for (uint32_t i = threadIdx.x; i < kTsBuckets; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < m; e += (uint64_t)gridDim.x * blockDim.x)
+        atomicAdd(&h[min(ts[e] >> shift, kTsBuckets - 1)], 1u);
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < kTsBuckets; i += blockDim.x)
+        if (h[i]) atomicAdd(&hist[i], (unsigned long long)h[i]);
+}
+}  // namespace
+
+int ts_histogram(tripoll_graph* g) {
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!g->ts_hist.empty() || !g->m) return TRIPOLL_OK;
+    int dev = -1;
+    TP_CUDA(cudaGetDevice(&dev));
+    if (dev != g->device) return TRIPOLL_OK;
+    cudaStream_t s;
+    TP_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    Scratch buf;
+    int rc = TRIPOLL_OK;
+    unsigned tmax = 0;
+    std::vector<uint64_t> h(kTsBuckets, 0);
+    uint32_t shift = 0;
+    do {
+        cudaError_t e = buf.alloc(8 + kTsBuckets * 8, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(buf.ptr, 0, 8 + kTsBuckets * 8, s);
+        if (e != cudaSuccess) { rc = ::tp::cuda_fail(e, "timestamp histogram buffer"); break; }
+        unsigned* mx = buf.as<unsigned>();
+        unsigned long long* hist = reinterpret_cast<unsigned long long*>(buf.as<unsigned char>() + 8);
+        ts_max_kernel<<<grid_n(g->m), 256, 0, s>>>(g->ts, g->m, mx); ::tp::note_launch();
+        if (cudaMemcpyAsync(&tmax, mx, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) { rc = fail(TRIPOLL_ERR_CUDA, "timestamp maximum"); break; }
+        while (shift < 32 && (tmax >> shift) >= kTsBuckets) ++shift;  // kTsBuckets buckets cover [0, tmax]
+        ts_hist_kernel<<<grid_n(g->m), 256, 0, s>>>(g->ts, g->m, shift, hist); ::tp::note_launch();
+        if (cudaMemcpyAsync(h.data(), hist, kTsBuckets * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) { rc = fail(TRIPOLL_ERR_CUDA, "timestamp histogram"); break; }
+    } while (false);
+    buf.release();
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+    if (rc) return rc;
+    g->ts_shift = shift;
+    g->ts_hist.swap(h);
+    return TRIPOLL_OK;
 }
 
 // Launch the survey kernels accumulating into `acc` (zeroed by the caller).
@@ -427,10 +496,6 @@ int launch_survey(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_
         TP_CUDA(vx.alloc(words * 8, s));
         TP_CUDA(vcnt.alloc(words * 4, s));
         TP_CUDA(vpre.alloc(words * 4, s));
-        TP_CUDA(vcol.alloc((m + kColPad) * 4, s));
-        TP_CUDA(vts.alloc((m + kColPad) * 4, s));
-        if (g->el) TP_CUDA(vel.alloc(m + kColPad, s));
-        if (kinds & TRIPOLL_EDGE_LOCAL) TP_CUDA(vorig.alloc(m * 4, s));
         TP_CUDA(vtmp.alloc(window_scan_bytes(m), s));
         view_bits_kernel<<<grid_n(words * 32), 256, 0, s>>>(g->ts, m, words, t_lo, t_hi, vx.as<uint2>(),
                                                             vcnt.as<uint32_t>()); ::tp::note_launch();
@@ -438,6 +503,17 @@ int launch_survey(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_
         if ((rc = prim::scan<uint32_t, false>(prim::Load<uint32_t, uint32_t>{vcnt.as<uint32_t>(), words},
                                               vpre.as<uint32_t>(), words, vtmp.ptr, s)))
             return rc;
+        // the in-window edges (the last word's prefix and count), read back to size the view to them: the
+        // same edges are the in-window in-edges
+        uint32_t tail[2] = {0, 0};
+        TP_CUDA(cudaMemcpyAsync(&tail[0], vpre.as<uint32_t>() + words - 1, 4, cudaMemcpyDeviceToHost, s));
+        TP_CUDA(cudaMemcpyAsync(&tail[1], vcnt.as<uint32_t>() + words - 1, 4, cudaMemcpyDeviceToHost, s));
+        TP_CUDA(cudaStreamSynchronize(s));
+        const uint64_t mv = (uint64_t)tail[0] + tail[1];
+        TP_CUDA(vcol.alloc((mv + kColPad) * 4, s));
+        TP_CUDA(vts.alloc((mv + kColPad) * 4, s));
+        if (g->el) TP_CUDA(vel.alloc(mv + kColPad, s));
+        if (kinds & TRIPOLL_EDGE_LOCAL) TP_CUDA(vorig.alloc(std::max<uint64_t>(mv, 1) * 4, s));
         view_prefix_kernel<<<grid_n(words), 256, 0, s>>>(vpre.as<uint32_t>(), words, vx.as<uint2>()); ::tp::note_launch();
         window_view_kernel<<<grid_n(m), 256, 0, s>>>(g->col, g->ts, g->el, vx.as<uint2>(), m, t_lo, t_hi,
                                                      vcol.as<uint32_t>(), vts.as<uint32_t>(),
@@ -446,9 +522,9 @@ int launch_survey(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_
         TP_CUDA(cudaGetLastError());
         // the in-edges in the window, their positions in the view (the counts and the scan reuse vcnt and vpre)
         TP_CUDA(ix.alloc(words * 8, s));
-        TP_CUDA(vin.alloc(m * sizeof(InEdge), s));
+        TP_CUDA(vin.alloc(std::max<uint64_t>(mv, 1) * sizeof(InEdge), s));
         const bool need_e = a.restricted || (F & F_EXTRA);  // the kernels read vin_e only then
-        if (need_e) TP_CUDA(vine.alloc(m * 4, s));
+        if (need_e) TP_CUDA(vine.alloc(std::max<uint64_t>(mv, 1) * 4, s));
         in_view_bits_kernel<<<grid_n(words * 32), 256, 0, s>>>(g->in_edge, m, words, t_lo, t_hi, ix.as<uint2>(),
                                                                vcnt.as<uint32_t>()); ::tp::note_launch();
         if ((rc = prim::scan<uint32_t, false>(prim::Load<uint32_t, uint32_t>{vcnt.as<uint32_t>(), words},
