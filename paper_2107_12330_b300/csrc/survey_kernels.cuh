@@ -399,6 +399,29 @@ __device__ __forceinline__ void probe_quad(const QTable<PosT>& T, const uint32_t
     }
 }
 
+// Rank bitmap of a staged part of Adj+(q) whose values lie in [vlo, vlo + span): bit r - vlo is set
+// for every staged r, and pre[w] counts the set bits of the words before w, so the staged index of a
+// set bit (the entries are sorted and all staged) is pre[w] + the set bits below it in its word.  A
+// block item uses it instead of the hash table when the span fits (span = 0: the hash table), which
+// in the degree order is the common case: a middle vertex's out-neighbours have higher degree and sit
+// together near the end of the order.
+struct RankBitmap {
+    const uint32_t* bm;
+    const uint32_t* pre;
+    uint32_t vlo, span;
+};
+
+__device__ __forceinline__ void probe_quad_bm(const RankBitmap& B, const uint32_t (&r)[4], const bool (&act)[4],
+                                              int (&pos)[4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const uint32_t b = r[i] - B.vlo;  // below vlo wraps to >= span
+        const uint32_t w = (act[i] && b < B.span) ? B.bm[b >> 5] : 0u;
+        const uint32_t sh = b & 31u;
+        pos[i] = ((w >> sh) & 1u) ? (int)(B.pre[b >> 5] + __popc(w & ((1u << sh) - 1u))) : -1;
+    }
+}
+
 // ---- in-edges of the item, staged ------------------------------------------------------------
 
 // Per in-edge (p,q) of the item: the segment [j0, jend) of Adj+(p) to check
@@ -616,11 +639,11 @@ __device__ __forceinline__ void push_quad(const int (&pos)[4], uint32_t e0, uint
 // 16-byte quad at a time.
 // The in-edge slots a chunk spans are found from the previous chunk's with
 // one ballot.  Hits are queued and folded 32 at a time, one per lane.
-template <int F, class PosT>
+template <int F, bool BM, class PosT>
 __device__ __forceinline__ void scan_flat(const GraphDev& g, const SurveyArgs& a, const QTable<PosT>& T,
-                                          const InStage& S, const HitQueue& H, uint32_t n_in, uint32_t f_begin,
-                                          uint32_t f_end, uint32_t qbase, uint32_t q, uint32_t l_q, uint32_t d_q,
-                                          MirrorWord* s_tab, unsigned long long* grec,
+                                          const RankBitmap& B, const InStage& S, const HitQueue& H, uint32_t n_in,
+                                          uint32_t f_begin, uint32_t f_end, uint32_t qbase, uint32_t q, uint32_t l_q,
+                                          uint32_t d_q, MirrorWord* s_tab, unsigned long long* grec,
                                           unsigned long long& cnt) {
     const uint32_t lane = threadIdx.x & 31;
     TriMeta t = {};
@@ -678,7 +701,8 @@ __device__ __forceinline__ void scan_flat(const GraphDev& g, const SurveyArgs& a
 #pragma unroll
                 for (int i = 0; i < 4; ++i) act[i] = ec + i >= lo[u] && ec + i < hi[u];
                 int pos[4];
-                probe_quad(T, rr, act, pos);
+                if (BM && B.span) probe_quad_bm(B, rr, act, pos);
+                else probe_quad(T, rr, act, pos);
                 push_quad<F>(pos, ec, ks[u], nq, g, a, T, S, H, t, s_tab, grec, cnt);
             }
         }
@@ -763,6 +787,9 @@ __global__ void __launch_bounds__(kBlockThreads, CHUNK <= kBlockChunk ? 5 : 3)
     survey_block_kernel(GraphDev g, const WorkItem* __restrict__ items,
                                                                      uint32_t n_items, SurveyArgs a) {
     constexpr uint32_t kBlockTable = kTableFactor * CHUNK;
+    // the rank bitmap and its prefix share the table's key array; each thread's words are consecutive
+    constexpr uint32_t kBmPerThread = kBlockTable / 2 / kBlockThreads;
+    constexpr uint32_t kBmWords = kBmPerThread * kBlockThreads;
     extern __shared__ __align__(16) unsigned char smem[];
     static_assert(kBlockThreads == prim::kThreads, "block scan width");
     __shared__ uint32_t scan_tmp[kWarps];
@@ -826,14 +853,49 @@ __global__ void __launch_bounds__(kBlockThreads, CHUNK <= kBlockChunk ? 5 : 3)
                 continue;
             }
         }
-        T.size = view_table_size(len, g.vidx != nullptr, kBlockTable);
-        const uint32_t tsize = T.size;
-        for (uint32_t i = threadIdx.x; i < tsize; i += blockDim.x) T.key[i] = kEmpty;
-        __syncthreads();
-        table_fill<F>(g, a, T, qbase, len, threadIdx.x, blockDim.x);
         const bool chunked = item.flags & 1u;
-        const uint32_t vlo = chunked ? __ldg(&g.col[qbase]) : 0u;
-        const uint32_t vhi = chunked ? __ldg(&g.col[qbase + len - 1]) : 0xFFFFFFFFu;
+        const uint32_t first = __ldg(&g.col[qbase]), last = __ldg(&g.col[qbase + len - 1]);
+        const uint32_t vlo = chunked ? first : 0u;
+        const uint32_t vhi = chunked ? last : 0xFFFFFFFFu;
+        // a rank bitmap when the part's values span few positions and every entry is staged (a window view,
+        // or no window); else the hash table
+        RankBitmap B{T.key, T.key + kBmWords, first, last - first + 1};
+        if (!(g.vidx || (a.t_lo == 0 && a.t_hi == 0xFFFFFFFFu)) || B.span > kBmWords * 32u) B.span = 0;
+        if (B.span) {
+            uint32_t* bm = T.key;
+            uint32_t* pre = T.key + kBmWords;
+            const uint32_t nw = (B.span + 31) >> 5;
+            for (uint32_t w = threadIdx.x; w < nw; w += blockDim.x) bm[w] = 0;
+            __syncthreads();
+            for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) {
+                const uint32_t r = __ldg(&g.col[qbase + i]);
+                atomicOr(&bm[(r - first) >> 5], 1u << ((r - first) & 31u));
+                if (F & F_TS) T.ts[i] = __ldg(&g.ts[qbase + i]);
+                if (F & F_EL) T.el[i] = __ldg(&g.el[qbase + i]);
+                if (F & F_VL) T.vl[i] = __ldg(&g.vl[r]);
+                if (F & F_EXTRA) T.deg[i] = __ldg(&g.deg[r]);
+            }
+            __syncthreads();
+            // pre: set bits before each word; a thread takes kBmPerThread consecutive words
+            const uint32_t w0 = threadIdx.x * kBmPerThread;
+            uint32_t c = 0;
+#pragma unroll
+            for (uint32_t j = 0; j < kBmPerThread; ++j) c += (w0 + j < nw) ? __popc(bm[w0 + j]) : 0u;
+            uint32_t total_bits;
+            uint32_t run = prim::block_exclusive_scan(c, scan_tmp, &total_bits);
+#pragma unroll
+            for (uint32_t j = 0; j < kBmPerThread; ++j)
+                if (w0 + j < nw) {
+                    pre[w0 + j] = run;
+                    run += __popc(bm[w0 + j]);
+                }
+        } else {
+            T.size = view_table_size(len, g.vidx != nullptr, kBlockTable);
+            const uint32_t tsize = T.size;
+            for (uint32_t i = threadIdx.x; i < tsize; i += blockDim.x) T.key[i] = kEmpty;
+            __syncthreads();
+            table_fill<F>(g, a, T, qbase, len, threadIdx.x, blockDim.x);
+        }
         const uint32_t l_q = (F & F_VL) ? __ldg(&g.vl[q]) : 0u;
         const uint32_t d_q = (F & F_EXTRA) ? __ldg(&g.deg[q]) : 0u;
         const uint32_t warp = threadIdx.x >> 5;
@@ -850,7 +912,7 @@ __global__ void __launch_bounds__(kBlockThreads, CHUNK <= kBlockChunk ? 5 : 3)
             __syncthreads();
             const uint32_t f_begin = (uint32_t)(((uint64_t)s_total * warp) / kWarps);
             const uint32_t f_end = (uint32_t)(((uint64_t)s_total * (warp + 1)) / kWarps);
-            scan_flat<F>(g, a, T, S, H, n_in, f_begin, f_end, qbase, q, l_q, d_q, s_tab, grec, cnt);
+            scan_flat<F, true>(g, a, T, B, S, H, n_in, f_begin, f_end, qbase, q, l_q, d_q, s_tab, grec, cnt);
         }
     }
     if (grec_prev) flush_count(cnt, a, s_tab, grec_prev);
@@ -955,7 +1017,8 @@ __global__ void __launch_bounds__(kBlockThreads, 5) survey_warp_kernel(GraphDev 
             HitQueue H;
             H.idx = ws.qidx;
             H.pk = ws.qpk;
-            scan_flat<F>(g, a, T, S, H, n_in, 0, total, qbase + c0, q, l_q, d_q, s_tab, grec, cnt);
+            scan_flat<F, false>(g, a, T, RankBitmap{nullptr, nullptr, 0u, 0u}, S, H, n_in, 0, total, qbase + c0, q,
+                                l_q, d_q, s_tab, grec, cnt);
         }
     }
     if (grec_prev) flush_count(cnt, a, s_tab, grec_prev);
