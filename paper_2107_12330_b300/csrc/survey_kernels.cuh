@@ -7,8 +7,9 @@
 // of its edges (q,r) and the labels of the r, is staged once in shared memory
 // as an open-addressing hash table, and then every in-edge (p,q) streams the
 // suffix of Adj+(p) after q from HBM and probes each candidate r against it
-// -- one probe per wedge (p,q,r), the wedge check of Sec. 3.  A hit is a
-// triangle; its six metadata items (Sec. 3) are the (p,q) edge's (read once
+// -- one probe per wedge (p,q,r), the wedge check of Sec. 3.  (A block item
+// whose staged out-list spans few positions uses a rank bitmap over the span
+// instead of the hash table.)  A hit is a triangle; its six metadata items (Sec. 3) are the (p,q) edge's (read once
 // per in-edge), the (p,r) edge's (gathered at the hit position), and the
 // (q,r) edge's plus vertex r's (from shared memory).
 //
