@@ -9,9 +9,10 @@
 // suffix of Adj+(p) after q from HBM and probes each candidate r against it
 // -- one probe per wedge (p,q,r), the wedge check of Sec. 3.  (A block item
 // whose staged out-list spans few positions uses a rank bitmap over the span
-// instead of the hash table.)  A hit is a triangle; its six metadata items (Sec. 3) are the (p,q) edge's (read once
-// per in-edge), the (p,r) edge's (gathered at the hit position), and the
-// (q,r) edge's plus vertex r's (from shared memory).
+// instead of the hash table.)  A hit is a triangle; its six metadata items
+// (Sec. 3) are the (p,q) edge's (read once per in-edge), the (p,r) edge's
+// (gathered at the hit position), and the (q,r) edge's plus vertex r's (from
+// shared memory).
 //
 // Three kernels split the middle vertices by |Adj+(q)|: a warp-per-item kernel
 // for out-lists of up to kWarpPlanQ entries (each warp its own table, staging
