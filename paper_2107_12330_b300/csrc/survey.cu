@@ -11,7 +11,7 @@
 namespace tp {
 namespace sv {
 #define TP_EXTERN_LAUNCH(F)                                                                               \
-    extern template void launch_f<F>(const tripoll_graph*, const GraphDev&, const SurveyArgs&, cudaStream_t, \
+    extern template void launch_f<F>(const ItemLists&, const GraphDev&, const SurveyArgs&, cudaStream_t, \
                                      int, cudaEvent_t*);
 TP_EXTERN_LAUNCH(0) TP_EXTERN_LAUNCH(1) TP_EXTERN_LAUNCH(2) TP_EXTERN_LAUNCH(3) TP_EXTERN_LAUNCH(4)
 TP_EXTERN_LAUNCH(5) TP_EXTERN_LAUNCH(6) TP_EXTERN_LAUNCH(7) TP_EXTERN_LAUNCH(8) TP_EXTERN_LAUNCH(9)
@@ -137,7 +137,7 @@ __global__ void plan_fill_kernel(const uint64_t* __restrict__ off, const uint64_
                 it.in_lo = ilo + (uint32_t)s;
                 it.in_hi = ilo + (uint32_t)umin64(di, s + per);
                 it.flags = chunked ? 1u : 0u;
-                it.pad0 = it.pad1 = 0;
+                it.vpos = it.pad = 0;
                 dst[o++] = it;
             }
         }
@@ -234,6 +234,31 @@ __global__ void in_view_kernel(const InEdge* __restrict__ in_edge, const uint2* 
         vin[at] = v;
         if (vin_e) vin_e[at] = ie.e;
     }
+}
+
+// Work items in a window view's positions: the staged part of Adj+(q) and the in-edge range translated
+// through the two indexes, and keep[i] = 1 unless the item has no in-window entry or in-edge (it could
+// close no triangle).
+__global__ void view_items_kernel(const WorkItem* __restrict__ items, uint64_t n, const uint64_t* __restrict__ off,
+                                  const uint2* __restrict__ vidx, const uint2* __restrict__ iidx,
+                                  WorkItem* __restrict__ out, uint32_t* __restrict__ keep) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        WorkItem it = items[i];
+        const uint32_t p0 = (uint32_t)off[it.q] + it.qlo;
+        const uint32_t b0 = view_pos(vidx, p0);
+        it.qlen = view_pos(vidx, p0 + it.qlen) - b0;
+        it.vpos = b0;
+        it.in_lo = view_pos(iidx, it.in_lo);
+        it.in_hi = view_pos(iidx, it.in_hi);
+        out[i] = it;
+        keep[i] = (it.qlen > 0 && it.in_hi > it.in_lo) ? 1u : 0u;
+    }
+}
+
+__global__ void scatter_items_kernel(const WorkItem* __restrict__ tmp, const uint32_t* __restrict__ keep,
+                                     const uint32_t* __restrict__ at, uint64_t n, WorkItem* __restrict__ out) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        if (keep[i]) out[at[i]] = tmp[i];
 }
 
 uint64_t view_words(uint64_t m) { return (m >> 5) + 1; }
@@ -349,7 +374,13 @@ uint64_t window_view_bytes(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo
     }
     const uint64_t r = 256;  // pool rounding per allocation
     const uint64_t w = view_words(m);
-    return 2 * (w * 8 + r) + 2 * (w * 4 + r) + window_scan_bytes(m) + r + 2 * ((mv + kColPad) * 4 + r) +
+    uint64_t items = 0, it_max = 1;  // the translated item lists: temporaries, flags, positions, the lists
+    for (uint64_t n : {g->n_items_warp}) {
+        if (n) items += 2 * (n * sizeof(WorkItem) + r) + 2 * ((n + 1) * 4 + r);
+        it_max = std::max(it_max, n + 1);
+    }
+    items += prim::scan_scratch_bytes(it_max) + r;
+    return items + 2 * (w * 8 + r) + 4 * (w * 4 + r) + window_scan_bytes(m) + r + 2 * ((mv + kColPad) * 4 + r) +
            (g->el ? mv + kColPad + r : 0) + (std::max<uint64_t>(mv, 1) * sizeof(InEdge) + r) +
            (std::max<uint64_t>(mv, 1) * 4 + r) + ((kinds & TRIPOLL_EDGE_LOCAL) ? std::max<uint64_t>(mv, 1) * 4 + r : 0);
 }
@@ -466,6 +497,7 @@ int launch_survey(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_
         }
         a.move_block_log2 = (uint8_t)kb;
         a.move_warp_log2 = (uint8_t)kw;
+        a.view_items = 0;
     }
     const bool window = !(t_lo == 0 && t_hi == 0xFFFFFFFFu);
     int F = 0;
@@ -490,7 +522,9 @@ int launch_survey(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_
     }
     mark(ev, 0, s);
     GraphDev gd = g->dev();
-    Scratch vx, vcnt, vpre, vcol, vts, vel, vorig, vtmp, ix, vin, vine;  // released (stream-ordered) after the kernels
+    // released (stream-ordered) after the kernels
+    Scratch vx, vcnt, vpre, vcol, vts, vel, vorig, vtmp, ix, icnt, ipre, vin, vine, iscan, ilist[3];
+    ItemLists L = {{g->items_warp, g->items_block, g->items_big}, {g->n_items_warp, g->n_items_block, g->n_items_big}};
     if (window && window_view && g->m) {
         const uint64_t m = g->m, words = view_words(m);
         TP_CUDA(vx.alloc(words * 8, s));
@@ -503,37 +537,74 @@ int launch_survey(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_
         if ((rc = prim::scan<uint32_t, false>(prim::Load<uint32_t, uint32_t>{vcnt.as<uint32_t>(), words},
                                               vpre.as<uint32_t>(), words, vtmp.ptr, s)))
             return rc;
-        // the in-window edges (the last word's prefix and count), read back to size the view to them: the
-        // same edges are the in-window in-edges
-        uint32_t tail[2] = {0, 0};
-        TP_CUDA(cudaMemcpyAsync(&tail[0], vpre.as<uint32_t>() + words - 1, 4, cudaMemcpyDeviceToHost, s));
-        TP_CUDA(cudaMemcpyAsync(&tail[1], vcnt.as<uint32_t>() + words - 1, 4, cudaMemcpyDeviceToHost, s));
+        view_prefix_kernel<<<grid_n(words), 256, 0, s>>>(vpre.as<uint32_t>(), words, vx.as<uint2>()); ::tp::note_launch();
+        // the in-window in-edge records' index, with counts and prefixes of its own (vcnt and vpre keep
+        // the edges' for the read-back below)
+        TP_CUDA(ix.alloc(words * 8, s));
+        TP_CUDA(icnt.alloc(words * 4, s));
+        TP_CUDA(ipre.alloc(words * 4, s));
+        in_view_bits_kernel<<<grid_n(words * 32), 256, 0, s>>>(g->in_edge, m, words, t_lo, t_hi, ix.as<uint2>(),
+                                                               icnt.as<uint32_t>()); ::tp::note_launch();
+        if ((rc = prim::scan<uint32_t, false>(prim::Load<uint32_t, uint32_t>{icnt.as<uint32_t>(), words},
+                                              ipre.as<uint32_t>(), words, vtmp.ptr, s)))
+            return rc;
+        view_prefix_kernel<<<grid_n(words), 256, 0, s>>>(ipre.as<uint32_t>(), words, ix.as<uint2>()); ::tp::note_launch();
+        // the warp kernel's work items in view positions, the empty ones marked for leaving out (the block
+        // kernels translate their few large items themselves)
+        const uint64_t n_it[3] = {g->n_items_warp, 0, 0};
+        const WorkItem* its[3] = {g->items_warp, g->items_block, g->items_big};
+        Scratch itmp[3], ikeep[3], iat[3];
+        uint64_t it_max = 1;
+        for (int k = 0; k < 3; ++k) it_max = std::max(it_max, n_it[k] + 1);
+        TP_CUDA(iscan.alloc(prim::scan_scratch_bytes(it_max), s));
+        for (int k = 0; k < 3; ++k) {
+            if (!n_it[k]) continue;
+            TP_CUDA(itmp[k].alloc(n_it[k] * sizeof(WorkItem), s));
+            TP_CUDA(ikeep[k].alloc((n_it[k] + 1) * 4, s));
+            TP_CUDA(iat[k].alloc((n_it[k] + 1) * 4, s));
+            TP_CUDA(cudaMemsetAsync(ikeep[k].as<uint32_t>() + n_it[k], 0, 4, s));
+            view_items_kernel<<<grid_n(n_it[k]), 256, 0, s>>>(its[k], n_it[k], g->off, vx.as<uint2>(), ix.as<uint2>(),
+                                                              itmp[k].as<WorkItem>(), ikeep[k].as<uint32_t>()); ::tp::note_launch();
+            if ((rc = prim::scan<uint32_t, false>(prim::Load<uint32_t, uint32_t>{ikeep[k].as<uint32_t>(), n_it[k] + 1},
+                                                  iat[k].as<uint32_t>(), n_it[k] + 1, iscan.ptr, s)))
+                return rc;
+        }
+        // one read-back sizes the view (the in-window edges: the last word's prefix and count; the same edges
+        // are the in-window in-edges) and the item lists that are left
+        uint32_t back[5] = {0, 0, 0, 0, 0};
+        TP_CUDA(cudaMemcpyAsync(&back[0], vpre.as<uint32_t>() + words - 1, 4, cudaMemcpyDeviceToHost, s));
+        TP_CUDA(cudaMemcpyAsync(&back[1], vcnt.as<uint32_t>() + words - 1, 4, cudaMemcpyDeviceToHost, s));
+        for (int k = 0; k < 3; ++k)
+            if (n_it[k]) TP_CUDA(cudaMemcpyAsync(&back[2 + k], iat[k].as<uint32_t>() + n_it[k], 4, cudaMemcpyDeviceToHost, s));
         TP_CUDA(cudaStreamSynchronize(s));
-        const uint64_t mv = (uint64_t)tail[0] + tail[1];
+        const uint64_t mv = (uint64_t)back[0] + back[1];
         TP_CUDA(vcol.alloc((mv + kColPad) * 4, s));
         TP_CUDA(vts.alloc((mv + kColPad) * 4, s));
         if (g->el) TP_CUDA(vel.alloc(mv + kColPad, s));
         if (kinds & TRIPOLL_EDGE_LOCAL) TP_CUDA(vorig.alloc(std::max<uint64_t>(mv, 1) * 4, s));
-        view_prefix_kernel<<<grid_n(words), 256, 0, s>>>(vpre.as<uint32_t>(), words, vx.as<uint2>()); ::tp::note_launch();
         window_view_kernel<<<grid_n(m), 256, 0, s>>>(g->col, g->ts, g->el, vx.as<uint2>(), m, t_lo, t_hi,
                                                      vcol.as<uint32_t>(), vts.as<uint32_t>(),
                                                      g->el ? vel.as<uint8_t>() : nullptr,
                                                      vorig.as<uint32_t>()); ::tp::note_launch();
         TP_CUDA(cudaGetLastError());
-        // the in-edges in the window, their positions in the view (the counts and the scan reuse vcnt and vpre)
-        TP_CUDA(ix.alloc(words * 8, s));
         TP_CUDA(vin.alloc(std::max<uint64_t>(mv, 1) * sizeof(InEdge), s));
         const bool need_e = a.restricted || (F & F_EXTRA);  // the kernels read vin_e only then
         if (need_e) TP_CUDA(vine.alloc(std::max<uint64_t>(mv, 1) * 4, s));
-        in_view_bits_kernel<<<grid_n(words * 32), 256, 0, s>>>(g->in_edge, m, words, t_lo, t_hi, ix.as<uint2>(),
-                                                               vcnt.as<uint32_t>()); ::tp::note_launch();
-        if ((rc = prim::scan<uint32_t, false>(prim::Load<uint32_t, uint32_t>{vcnt.as<uint32_t>(), words},
-                                              vpre.as<uint32_t>(), words, vtmp.ptr, s)))
-            return rc;
-        view_prefix_kernel<<<grid_n(words), 256, 0, s>>>(vpre.as<uint32_t>(), words, ix.as<uint2>()); ::tp::note_launch();
         in_view_kernel<<<grid_n(m), 256, 0, s>>>(g->in_edge, ix.as<uint2>(), vx.as<uint2>(), m, t_lo, t_hi,
                                                  vin.as<InEdge>(), need_e ? vine.as<uint32_t>() : nullptr); ::tp::note_launch();
+        for (int k = 0; k < 3; ++k) {
+            if (!n_it[k]) continue;
+            L.items[k] = nullptr;
+            L.n[k] = back[2 + k];
+            if (!L.n[k]) continue;
+            TP_CUDA(ilist[k].alloc(L.n[k] * sizeof(WorkItem), s));
+            scatter_items_kernel<<<grid_n(n_it[k]), 256, 0, s>>>(itmp[k].as<WorkItem>(), ikeep[k].as<uint32_t>(),
+                                                                 iat[k].as<uint32_t>(), n_it[k],
+                                                                 ilist[k].as<WorkItem>()); ::tp::note_launch();
+            L.items[k] = ilist[k].as<WorkItem>();
+        }
         TP_CUDA(cudaGetLastError());
+        a.view_items = 1;
         gd.col = vcol.as<uint32_t>();
         gd.ts = vts.as<uint32_t>();
         gd.el = g->el ? vel.as<uint8_t>() : nullptr;
@@ -543,7 +614,7 @@ int launch_survey(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_
         gd.iidx = ix.as<uint2>();
         gd.vin_e = need_e ? vine.as<uint32_t>() : nullptr;
     }
-    kLaunch[F](g, gd, a, s, sms, ev);
+    kLaunch[F](L, gd, a, s, sms, ev);
     TP_CUDA(cudaGetLastError());
     return TRIPOLL_OK;
 }

@@ -4,13 +4,13 @@
 
 namespace tp {
 namespace sv {
-template void launch_f<8>(const tripoll_graph*, const GraphDev&, const SurveyArgs&, cudaStream_t, int, cudaEvent_t*);
-template void launch_f<9>(const tripoll_graph*, const GraphDev&, const SurveyArgs&, cudaStream_t, int, cudaEvent_t*);
-template void launch_f<10>(const tripoll_graph*, const GraphDev&, const SurveyArgs&, cudaStream_t, int, cudaEvent_t*);
-template void launch_f<11>(const tripoll_graph*, const GraphDev&, const SurveyArgs&, cudaStream_t, int, cudaEvent_t*);
-template void launch_f<12>(const tripoll_graph*, const GraphDev&, const SurveyArgs&, cudaStream_t, int, cudaEvent_t*);
-template void launch_f<13>(const tripoll_graph*, const GraphDev&, const SurveyArgs&, cudaStream_t, int, cudaEvent_t*);
-template void launch_f<14>(const tripoll_graph*, const GraphDev&, const SurveyArgs&, cudaStream_t, int, cudaEvent_t*);
-template void launch_f<15>(const tripoll_graph*, const GraphDev&, const SurveyArgs&, cudaStream_t, int, cudaEvent_t*);
+template void launch_f<8>(const ItemLists&, const GraphDev&, const SurveyArgs&, cudaStream_t, int, cudaEvent_t*);
+template void launch_f<9>(const ItemLists&, const GraphDev&, const SurveyArgs&, cudaStream_t, int, cudaEvent_t*);
+template void launch_f<10>(const ItemLists&, const GraphDev&, const SurveyArgs&, cudaStream_t, int, cudaEvent_t*);
+template void launch_f<11>(const ItemLists&, const GraphDev&, const SurveyArgs&, cudaStream_t, int, cudaEvent_t*);
+template void launch_f<12>(const ItemLists&, const GraphDev&, const SurveyArgs&, cudaStream_t, int, cudaEvent_t*);
+template void launch_f<13>(const ItemLists&, const GraphDev&, const SurveyArgs&, cudaStream_t, int, cudaEvent_t*);
+template void launch_f<14>(const ItemLists&, const GraphDev&, const SurveyArgs&, cudaStream_t, int, cudaEvent_t*);
+template void launch_f<15>(const ItemLists&, const GraphDev&, const SurveyArgs&, cudaStream_t, int, cudaEvent_t*);
 }  // namespace sv
 }  // namespace tp

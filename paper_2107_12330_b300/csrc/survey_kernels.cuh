@@ -115,11 +115,20 @@ struct SurveyArgs {
     // kernel, a warp of the warp kernel.  (These sit in what would otherwise be padding: a larger
     // argument block measurably slowed the survey kernels.)
     uint8_t move_block_log2, move_warp_log2;
-    Layout lay;  // (the argument block keeps 5 bytes of padding after the move periods)
+    // the warp kernel's items hold window-view positions already (vpos, qlen, in_lo, in_hi), none empty
+    uint8_t view_items;
+    Layout lay;  // (the argument block keeps 4 bytes of padding after the flags)
     unsigned long long* out;  // accumulator: one record, or num_graphs records (batched)
     uint32_t* counters;       // item counters of the three kernels; F_MULTI: [4] A, [5] B, then the bounds
 };
 static_assert(sizeof(SurveyArgs) == 128, "kernel argument block of the survey kernels");
+
+// The work item lists a survey launch runs (warp, block, long-list kernels): the graph's, or for the
+// warp kernel their translation into a window view's positions with the empty items left out.
+struct ItemLists {
+    const WorkItem* items[3];
+    uint64_t n[3];
+};
 
 // Resident blocks per SM of a kernel at a dynamic shared-memory size (survey.cu).
 int blocks_per_sm(const void* kernel, size_t smem);
@@ -971,10 +980,10 @@ __global__ void __launch_bounds__(kBlockThreads, 5) survey_warp_kernel(GraphDev 
             cnt = 0;
         }
         grec_prev = grec;
-        uint32_t qbase = (uint32_t)g.off[q];
+        uint32_t qbase = a.view_items ? item.vpos : (uint32_t)g.off[q];
         uint32_t len = item.qlen;
         uint32_t in_lo = item.in_lo, in_hi = item.in_hi;
-        if (g.vidx) {  // Adj+(q) in the window view
+        if (g.vidx && !a.view_items) {  // Adj+(q) in the window view
             const uint32_t b0 = view_pos(g.vidx, qbase);
             len = view_pos(g.vidx, qbase + len) - b0;
             qbase = b0;
@@ -1036,37 +1045,37 @@ inline void mark(cudaEvent_t* ev, int k, cudaStream_t s) {
 }
 
 template <int F>
-void launch_f(const tripoll_graph* g, const GraphDev& gd, const SurveyArgs& a, cudaStream_t s, int sms,
+void launch_f(const ItemLists& L, const GraphDev& gd, const SurveyArgs& a, cudaStream_t s, int sms,
               cudaEvent_t* ev) {
     mark(ev, 1, s);
-    if (g->n_items_warp) {
+    if (L.n[0]) {
         size_t sm = multi_bytes<F>() + mirror_bytes<F>(a.s_words) + kWarps * sizeof(WarpSmem);
         const int per = blocks_per_sm((const void*)survey_warp_kernel<F>, sm);
         uint64_t blocks = (uint64_t)per * sms;
-        blocks = std::min<uint64_t>(blocks, (g->n_items_warp + kWarps - 1) / kWarps);
-        survey_warp_kernel<F><<<(unsigned)blocks, kBlockThreads, sm, s>>>(gd, g->items_warp,
-                                                                         (uint32_t)g->n_items_warp, a); ::tp::note_launch();
+        blocks = std::min<uint64_t>(blocks, (L.n[0] + kWarps - 1) / kWarps);
+        survey_warp_kernel<F><<<(unsigned)blocks, kBlockThreads, sm, s>>>(gd, L.items[0],
+                                                                         (uint32_t)L.n[0], a); ::tp::note_launch();
     }
     mark(ev, 2, s);
-    if (g->n_items_block) {
+    if (L.n[1]) {
         size_t sm = multi_bytes<F>() + mirror_bytes<F>(a.s_words) + block_smem_fixed<F, kBlockChunk>();
         const int per = blocks_per_sm((const void*)survey_block_kernel<F, kBlockChunk, 1>, sm);
-        uint64_t blocks = std::min<uint64_t>((uint64_t)per * sms, g->n_items_block);
+        uint64_t blocks = std::min<uint64_t>((uint64_t)per * sms, L.n[1]);
         survey_block_kernel<F, kBlockChunk, 1><<<(unsigned)blocks, kBlockThreads, sm, s>>>(
-            gd, g->items_block, (uint32_t)g->n_items_block, a); ::tp::note_launch();
+            gd, L.items[1], (uint32_t)L.n[1], a); ::tp::note_launch();
     }
     mark(ev, 3, s);
-    if (g->n_items_big) {
+    if (L.n[2]) {
         size_t sm = multi_bytes<F>() + mirror_bytes<F>(a.s_words) + block_smem_fixed<F, kBigChunk>();
         const int per = blocks_per_sm((const void*)survey_block_kernel<F, kBigChunk, 2>, sm);
-        uint64_t blocks = std::min<uint64_t>((uint64_t)per * sms, g->n_items_big);
+        uint64_t blocks = std::min<uint64_t>((uint64_t)per * sms, L.n[2]);
         survey_block_kernel<F, kBigChunk, 2><<<(unsigned)blocks, kBlockThreads, sm, s>>>(
-            gd, g->items_big, (uint32_t)g->n_items_big, a); ::tp::note_launch();
+            gd, L.items[2], (uint32_t)L.n[2], a); ::tp::note_launch();
     }
     mark(ev, 4, s);
 }
 
-using LaunchFn = void (*)(const tripoll_graph*, const GraphDev&, const SurveyArgs&, cudaStream_t, int, cudaEvent_t*);
+using LaunchFn = void (*)(const ItemLists&, const GraphDev&, const SurveyArgs&, cudaStream_t, int, cudaEvent_t*);
 
 }  // namespace sv
 }  // namespace tp
