@@ -108,7 +108,7 @@ struct __align__(16) WorkItem {
     uint32_t in_lo;   // into in_edge[], absolute
     uint32_t in_hi;
     uint32_t flags;   // bit 0: chunked (restrict suffix to the staged value range)
-    uint32_t vpos;    // translated items only (a survey's window view): the part's first view position
+    uint32_t vpos;    // the part's first CSR position, off[q] + qlo (in a window view's positions once translated)
     uint32_t pad;
 };
 

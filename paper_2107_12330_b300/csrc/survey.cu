@@ -137,7 +137,8 @@ __global__ void plan_fill_kernel(const uint64_t* __restrict__ off, const uint64_
                 it.in_lo = ilo + (uint32_t)s;
                 it.in_hi = ilo + (uint32_t)umin64(di, s + per);
                 it.flags = chunked ? 1u : 0u;
-                it.vpos = it.pad = 0;
+                it.vpos = (uint32_t)(off[q] + c);
+                it.pad = 0;
                 dst[o++] = it;
             }
         }
@@ -239,12 +240,12 @@ __global__ void in_view_kernel(const InEdge* __restrict__ in_edge, const uint2* 
 // Work items in a window view's positions: the staged part of Adj+(q) and the in-edge range translated
 // through the two indexes, and keep[i] = 1 unless the item has no in-window entry or in-edge (it could
 // close no triangle).
-__global__ void view_items_kernel(const WorkItem* __restrict__ items, uint64_t n, const uint64_t* __restrict__ off,
-                                  const uint2* __restrict__ vidx, const uint2* __restrict__ iidx,
-                                  WorkItem* __restrict__ out, uint32_t* __restrict__ keep) {
+__global__ void view_items_kernel(const WorkItem* __restrict__ items, uint64_t n, const uint2* __restrict__ vidx,
+                                  const uint2* __restrict__ iidx, WorkItem* __restrict__ out,
+                                  uint32_t* __restrict__ keep) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
         WorkItem it = items[i];
-        const uint32_t p0 = (uint32_t)off[it.q] + it.qlo;
+        const uint32_t p0 = it.vpos;
         const uint32_t b0 = view_pos(vidx, p0);
         it.qlen = view_pos(vidx, p0 + it.qlen) - b0;
         it.vpos = b0;
@@ -563,7 +564,7 @@ int launch_survey(const tripoll_graph* g, uint32_t kinds, uint32_t t_lo, uint32_
             TP_CUDA(ikeep[k].alloc((n_it[k] + 1) * 4, s));
             TP_CUDA(iat[k].alloc((n_it[k] + 1) * 4, s));
             TP_CUDA(cudaMemsetAsync(ikeep[k].as<uint32_t>() + n_it[k], 0, 4, s));
-            view_items_kernel<<<grid_n(n_it[k]), 256, 0, s>>>(its[k], n_it[k], g->off, vx.as<uint2>(), ix.as<uint2>(),
+            view_items_kernel<<<grid_n(n_it[k]), 256, 0, s>>>(its[k], n_it[k], vx.as<uint2>(), ix.as<uint2>(),
                                                               itmp[k].as<WorkItem>(), ikeep[k].as<uint32_t>()); ::tp::note_launch();
             if ((rc = prim::scan<uint32_t, false>(prim::Load<uint32_t, uint32_t>{ikeep[k].as<uint32_t>(), n_it[k] + 1},
                                                   iat[k].as<uint32_t>(), n_it[k] + 1, iscan.ptr, s)))

@@ -848,7 +848,7 @@ __global__ void __launch_bounds__(kBlockThreads, CHUNK <= kBlockChunk ? 5 : 3)
             cnt = 0;
         }
         grec_prev = grec;
-        uint32_t qbase = (uint32_t)g.off[q] + item.qlo;
+        uint32_t qbase = item.vpos;
         uint32_t len = item.qlen;
         uint32_t in_lo = item.in_lo, in_hi = item.in_hi;
         if (g.vidx) {  // the item's part of Adj+(q) in the window view
@@ -980,7 +980,7 @@ __global__ void __launch_bounds__(kBlockThreads, 5) survey_warp_kernel(GraphDev 
             cnt = 0;
         }
         grec_prev = grec;
-        uint32_t qbase = a.view_items ? item.vpos : (uint32_t)g.off[q];
+        uint32_t qbase = item.vpos;
         uint32_t len = item.qlen;
         uint32_t in_lo = item.in_lo, in_hi = item.in_hi;
         if (g.vidx && !a.view_items) {  // Adj+(q) in the window view
