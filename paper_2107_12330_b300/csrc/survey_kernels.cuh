@@ -966,11 +966,13 @@ __global__ void __launch_bounds__(kBlockThreads, 5) survey_warp_kernel(GraphDev 
     unsigned long long* grec_prev = nullptr;
     uint32_t taken = 0;  // items this warp has taken (warp-uniform)
 
+    // each warp claims its next item while it surveys the current one
+    uint32_t next = 0;
+    if (lane == 0) next = atomicAdd(&a.counters[0], 1u);
     while (true) {
-        uint32_t it = 0;
-        if (lane == 0) it = atomicAdd(&a.counters[0], 1u);
-        it = __shfl_sync(0xffffffffu, it, 0);
+        const uint32_t it = __shfl_sync(0xffffffffu, next, 0);
         if (it >= n_items) break;
+        if (lane == 0) next = atomicAdd(&a.counters[0], 1u);
         if ((++taken & ((1u << a.move_warp_log2) - 1u)) == 0) move_mirror_warp<F>(s_tab, a.s_words, a.out);
         const WorkItem item = items[it];
         const uint32_t q = item.q;
