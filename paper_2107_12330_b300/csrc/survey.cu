@@ -157,7 +157,11 @@ unsigned grid_n(uint64_t items) {
 // same order <+.  Compacting col/ts/el to that subgraph before the wedge
 // checks removes the wedges (p,q),(p,r) whose (p,r) lies outside the window:
 // with a window holding a fraction f of the edges, the checks drop from about
-// f |W+| (in-place skipping of (p,q) and (q,r) only) to about f^2 |W+|.
+// f |W+| (in-place skipping of (p,q) and (q,r) only) to about f^2 |W+|.  The
+// in-edge records are compacted the same way (their suffix bounds translated
+// into view positions), and the warp kernel's work items are translated once,
+// the items with nothing in the window left out.  One read-back of the counts
+// sizes all of it.
 
 // The window view's index, first part: per 32 CSR positions (a warp), the in-window bits (into
 // vidx[w].y) and their count (the input of the scan that gives vidx[w].x).
